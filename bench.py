@@ -1,0 +1,334 @@
+"""Benchmark: p-BiCGStab time to a 1e-10 true relative residual on GB300.
+
+Workload (one "step" = one complete solve): 2D upwind convection-diffusion,
+1024 x 1024 grid (N = 1,048,576), cell Peclet 0.5, matrix stored as 5 FP64
+diagonals, Jacobi preconditioner, x* ~ U[0,1] (seed 2), b = A x*, x0 = 0,
+tol 1e-10 on ||b - A x|| / ||b||.  The headline variant is set by --precision
+(fp64 with periodic replacement every 100 iterations by default); the other
+variant is measured alongside.
+
+Prints ONE JSON line on rank 0.  --impl reference times the CPU oracle instead
+(a bounded sample of iterations, extrapolated with the oracle's iteration count
+stored in tests/golden/oracle_iterations_convdiff2d_1024.json).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "p-BiCGStab time to true rel. residual 1e-10 & HBM GB/s, mixed vs FP64"
+GRID = 1024
+GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations_convdiff2d_1024.json")
+
+
+# ----------------------------------------------------------------------------- byte model
+def bytes_per_row_iteration(precision: str, fmt: str = "dia", ndiag: int = 5, nnz_row: float = 5.0) -> float:
+    """Algorithmic bytes per row and iteration of the fused two-pass iteration
+    (Jacobi folded into the operator A D^{-1}, m and n formed on the fly, q, u, y
+    recomputed, neighbour gathers counted once):
+      pass A reads w k g l s z v r + D^{-1}, writes g s l z t;
+      pass B reads z x g k l r s w t r0 + D^{-1}, writes v x r k w;
+    28 vector streams (x read+written in FP64) plus two reads of the operator.
+    DIA: the folded operator stores ndiag-1 diagonals and D^{-1} replaces the unit
+    main diagonal, so operator + D^{-1} = ndiag values per row per pass."""
+    es = 8 if precision == "fp64" else 4
+    vec = 26 * es + 2 * 8            # x is FP64 in both modes
+    if fmt == "dia":
+        mat = 2 * ndiag * es
+    else:
+        mat = 2 * (nnz_row * (es + 4) + 4 + es)   # values + col + row_ptr + D^{-1}
+    return float(vec + mat)
+
+
+def bytes_per_row_replacement(precision: str, ndiag: int = 5) -> float:
+    """Eq. (rr) pass pair: R1 reads b, x, g, z + 2 FP64 operator reads, writes r k s l n;
+    R2 reads r, s, r0 + 2 folded operator reads, writes w z."""
+    es = 8 if precision == "fp64" else 4
+    r1 = 2 * 8 + es * 2 + 2 * ndiag * 8 + 5 * es
+    r2 = 3 * es + 2 * ndiag * es + 2 * es
+    return float(r1 + r2)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0],
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                s = float(f[1])
+                mx = float(f[2])
+            except ValueError:
+                continue
+            sm.append(s)
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        busy = [s for s in sm if mx and s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import testproblems as tp
+    import paper_1809_01948_gb300 as pb
+    pb.build()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    prob = tp.config2(GRID)
+    off, data = tp.csr_to_dia(prob.A)
+    dia = torch.from_numpy(data).to(dev)
+    b = torch.from_numpy(prob.b).to(dev)
+    n = prob.A.n
+    variants = {
+        "fp64": dict(precision="fp64", rr_period=100, rr_theta=0.0),
+        "mixed": dict(precision="mixed", rr_period=0, rr_theta=args.theta),
+    }
+    solvers = {k: pb.Solver(n, offsets=off.tolist(), dia=dia, precond="jacobi", tol=1e-10,
+                            max_it=args.max_it, **v) for k, v in variants.items()}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def one(name):
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, res = solvers[name].solve(b, x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res, x
+
+    results = {}
+    clocks = None
+    for name in (args.precision,) + tuple(k for k in variants if k != args.precision):
+        for _ in range(args.warmup):
+            one(name)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler() if name == args.precision else None
+        if sampler:
+            sampler.start()
+        times, ktimes, its, nrep, trues, stat = [], [], [], [], [], []
+        for _ in range(args.steps):
+            ms, res, x = one(name)
+            times.append(ms)
+            ktimes.append(res.time_ms)
+            its.append(res.iterations)
+            nrep.append(res.n_replacements)
+            trues.append(res.rel_res_true)
+            stat.append(res.status)
+        torch.cuda.synchronize()
+        if sampler:
+            clocks = sampler.stop()
+        if world > 1:
+            t = torch.tensor([sum(times)], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        else:
+            total = sum(times)
+        results[name] = dict(ms_per_solve=total / args.steps, kernel_ms=statistics.mean(ktimes),
+                             iterations=its[-1], n_replacements=nrep[-1], rel_res_true=max(trues),
+                             status=[pb.STATUS_NAMES[s] for s in stat][-1])
+
+    # end-to-end through the public API with host buffers (pinned)
+    head = results[args.precision]
+    b_pin = torch.from_numpy(prob.b).pin_memory()
+    x_pin = torch.zeros(n, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for k in range(max(1, args.steps)):
+        x_pin.zero_()
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, res = solvers[args.precision].solve_host(b_pin.numpy(), x_pin.numpy())
+        e2e_times.append((time.perf_counter() - t0) * 1e3)
+    e2e = {"value": statistics.mean(e2e_times), "unit": "ms", "h2d_bytes_per_step": 2 * 8 * n,
+           "d2h_bytes_per_step": 8 * n + 64}
+
+    # roofline of the dominant kernel (the persistent solver)
+    prec = args.precision
+    bpr = bytes_per_row_iteration(prec)
+    alg_bytes = n * (bpr * head["iterations"] + bytes_per_row_replacement(prec) * head["n_replacements"])
+    achieved = alg_bytes / (head["kernel_ms"] * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "bytes_per_row_iteration": bpr}
+    if prec == "fp64":
+        # FP64 arithmetic bound: ~42 FP64 FMA-class ops per row and iteration
+        flops = 2.0 * 42 * n * head["iterations"]
+        roof["fp64_alu"] = {"achieved_tflops": round(flops / (head["kernel_ms"] * 1e-3) / 1e12, 3),
+                            "peak_tflops_measured": 1.197}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args, head["iterations"], sample_iters=args.cpu_iters)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(head["ms_per_solve"], 4), "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms_per_solve"], 4),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": "convdiff2d_1024x1024_dia5_jacobi_tol1e-10", "n": n, "format": "DIA 5 diagonals FP64",
+                       "precision": prec, "replacement": variants[prec], "global_batch": 1 * world,
+                       "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps (256 MB write)"},
+            "iterations": head["iterations"], "n_replacements": head["n_replacements"],
+            "rel_res_true": head["rel_res_true"], "status": head["status"],
+            "iters_per_s": round(head["iterations"] / (head["kernel_ms"] * 1e-3), 1),
+            "kernel_ms": round(head["kernel_ms"], 4),
+            "variants": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                         for k, v in results.items()},
+            "roofline": roof, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 3 * args.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- CPU oracle arm
+_ORACLE_SNIPPET = r"""
+import json, sys, time, os
+sys.path.insert(0, %(root)r)
+import numpy as np
+import testproblems as tp
+from oracle import krylov
+prob = tp.config2(%(grid)d)
+A = prob.A.to_scipy()
+t0 = time.perf_counter()
+r = krylov.pbicgstab(A, prob.b, precond="jacobi", tol=1e-300, maxit=%(iters)d, rr_period=100)
+dt = time.perf_counter() - t0
+print(json.dumps({"seconds": dt, "iterations": r.iterations}))
+"""
+
+
+def _oracle_sample(iters: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", _ORACLE_SNIPPET % dict(root=ROOT, grid=GRID, iters=iters)],
+                         capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def _golden_iterations(default: int) -> int:
+    try:
+        return int(json.load(open(GOLDEN_ITERS))["fp64_rr100"]["iterations"])
+    except Exception:
+        return default
+
+
+def cpu_baseline(args, gpu_iterations: int, sample_iters: int = 40):
+    s = _oracle_sample(sample_iters)
+    per_it = s["seconds"] / s["iterations"]
+    iters = _golden_iterations(gpu_iterations)
+    return {"value": round(per_it * iters * 1e3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": "%d iterations of the FP64 numpy oracle on the full 1024x1024 system (%.1f s), "
+                      "extrapolated to %d iterations" % (s["iterations"], s["seconds"], iters),
+            "ms_per_iteration": round(per_it * 1e3, 3)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times = []
+    for _ in range(args.warmup):
+        _oracle_sample(args.cpu_iters)
+    per = []
+    for _ in range(args.steps):
+        s = _oracle_sample(args.cpu_iters)
+        per.append(s["seconds"] / s["iterations"])
+    iters = _golden_iterations(2000)
+    value = statistics.mean(per) * iters * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(value, 1), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "convdiff2d_1024x1024_dia5_jacobi_tol1e-10", "precision": "fp64",
+                       "replacement": {"rr_period": 100}},
+            "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": "%d iterations per step of the numpy oracle, extrapolated to %d iterations"
+                                       % (args.cpu_iters, iters)},
+            "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--theta", type=float, default=1e-3)
+    ap.add_argument("--max-it", type=int, default=20000)
+    ap.add_argument("--cpu-iters", type=int, default=40)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

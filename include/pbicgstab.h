@@ -1,0 +1,175 @@
+/*
+ * pbicgstab.h -- C ABI of libpbicgstab, a GB300 (sm_103a) implementation of the
+ * preconditioned pipelined BiCGStab method (p-BiCGStab) analysed in
+ * S. Cools, "Analyzing and improving maximal attainable accuracy in the
+ * communication hiding pipelined BiCGStab method", arXiv 1809.01948.
+ *
+ * Problem statement (Section 1): solve A x = b for a sparse, non-singular
+ * N x N matrix A, given b and an initial guess x0, with a preconditioner
+ * M^{-1} (Algorithm 2, "p-bicgstab(A, M^{-1}, b, x0)"), a tolerance on the
+ * recursively computed residual norm (Section 3.5) and a residual replacement
+ * policy (Section 3.6, Eq. rr).
+ *
+ * Conventions for every entry point:
+ *  - Every function returns a pbcg_status; PBCG_OK (0) on success.
+ *  - The library never aborts and never prints.  On failure the thread-local
+ *    message pbicgstab_last_error() describes the cause.
+ *  - "device" pointers are CUDA global-memory pointers of the current device;
+ *    "host" pointers are ordinary CPU memory.  Streams are cudaStream_t passed
+ *    as void* (NULL = the legacy default stream).
+ *  - Sizes: n < 2^31 - 1 rows, nnz < 2^31 - 1 stored entries (int32 indices).
+ *  - A context is bound to the stream given at creation; contexts are not
+ *    thread-safe.  Work is stream-ordered; a call blocks the host only when it
+ *    returns results in host memory (pbcg_result, host vectors).
+ */
+#ifndef PBICGSTAB_H
+#define PBICGSTAB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pbcg_status {
+  PBCG_OK = 0,             /* converged: ||r_i|| <= tol ||b|| and the true residual too   */
+  PBCG_INVALID_ARG = 1,    /* bad pointer, size, matrix structure or option; nothing ran  */
+  PBCG_CUDA_ERROR = 2,     /* a CUDA call failed; see pbicgstab_last_error()             */
+  PBCG_OUT_OF_MEMORY = 3,  /* device allocation failed                                   */
+  PBCG_NOT_CONVERGED = 4,  /* max_it iterations done without meeting the tolerance       */
+  PBCG_BREAKDOWN = 5,      /* a zero or non-finite alpha denominator, omega, (r0,r_i)    */
+  PBCG_STAGNATED = 6,      /* recursive residual met tol, true residual did not, no replacement policy */
+  PBCG_TIMEOUT = 7         /* a grid-wide wait inside a kernel exceeded timeout_ms       */
+} pbcg_status;
+
+typedef enum pbcg_format { PBCG_FMT_CSR = 0, PBCG_FMT_DIA = 1 } pbcg_format;
+typedef enum pbcg_dtype { PBCG_F64 = 0, PBCG_F32 = 1 } pbcg_dtype;
+typedef enum pbcg_precond_kind {
+  PBCG_PREC_NONE = 0,      /* M^{-1} = I (the paper's timing runs, Section 4.1)          */
+  PBCG_PREC_JACOBI = 1,    /* M^{-1} = D^{-1}, D = diag(A)                               */
+  PBCG_PREC_NEUMANN = 2    /* M^{-1} = sum_{j=0..d} (I - D^{-1}A)^j D^{-1}, degree d >= 1 */
+} pbcg_precond_kind;
+typedef enum pbcg_precision {
+  PBCG_FP64 = 0,           /* every vector, value and operation in FP64                  */
+  PBCG_MIXED = 1           /* FP32 values, SpMV, preconditioner and recurrences; FP64 x,
+                              b, dot-product results, alpha/beta/omega and replacement
+                              residual r = b - A x (FP64 values)                          */
+} pbcg_precision;
+
+/* Sparse matrix description.  All arrays are read once by pbicgstab_create,
+ * which keeps its own copies; the caller may free them afterwards.
+ *  CSR: row_ptr[n+1], col[nnz] (int32, device), val[nnz] (device, val_dtype).
+ *       Column indices within a row must be strictly increasing.
+ *  DIA: ndiag (1..16) diagonals, offsets[ndiag] (HOST, strictly increasing,
+ *       containing 0), val[ndiag*n] (device, val_dtype) with
+ *       val[d*n + i] = A[i, i + offsets[d]] (entries outside 0..n-1 ignored). */
+typedef struct pbcg_matrix {
+  int32_t format;          /* pbcg_format */
+  int32_t val_dtype;       /* pbcg_dtype  */
+  int64_t n;
+  int64_t nnz;             /* CSR only */
+  const int32_t* row_ptr;  /* CSR only, device */
+  const int32_t* col;      /* CSR only, device */
+  const void* val;         /* device */
+  int32_t ndiag;           /* DIA only */
+  int32_t reserved0;
+  const int32_t* offsets;  /* DIA only, host */
+} pbcg_matrix;
+
+typedef struct pbcg_precond {
+  int32_t kind;            /* pbcg_precond_kind */
+  int32_t degree;          /* Neumann degree d (1..8); ignored otherwise */
+} pbcg_precond;
+
+/* Number of doubles per iteration in the optional scalar history:
+ * [alpha_i, omega_i, beta_{i+1} (NaN on the last iteration), ||r_{i+1}|| / ||b||,
+ *  1.0 if a replacement (Eq. rr) happened in iteration i else 0.0, reserved...] */
+#define PBCG_HIST_STRIDE 8
+
+typedef struct pbcg_options {
+  int32_t precision;       /* pbcg_precision */
+  int32_t max_it;          /* > 0 */
+  double tol;              /* stop when ||r_i|| <= tol ||b|| (recursive, then verified) */
+  int32_t rr_period;       /* periodic replacement every P iterations while
+                              ||r_i|| >= sqrt(2^-52) ||r_0|| (Section 3.6); 0 = off    */
+  int32_t rr_auto;         /* reserved, must be 0 */
+  double rr_theta;         /* relative trigger: replace when ||r_i|| <= theta * (residual
+                              norm after the previous replacement); 0 = off            */
+  double timeout_ms;       /* limit of every grid-wide wait in the kernels; <= 0: 2000 */
+  int32_t record_iterates; /* K >= 0: write x_{i+1} to hist_x[i*n .. ] for i < K      */
+  int32_t hist_len;        /* capacity of hist_scalars, in iterations (0 = none)      */
+  double* hist_x;          /* device, K*n doubles, or NULL when K == 0                */
+  double* hist_scalars;    /* device, hist_len*PBCG_HIST_STRIDE doubles, or NULL      */
+  int32_t grid_blocks;     /* persistent grid size; 0 = automatic                     */
+  int32_t block_threads;   /* threads per block (multiple of 32, <= 1024); 0 = auto   */
+} pbcg_options;
+
+typedef struct pbcg_result {
+  int32_t status;          /* pbcg_status of the solve */
+  int32_t iterations;      /* completed iterations of Algorithm 2 */
+  int32_t n_replacements;  /* executed Eq. (rr) steps (periodic, relative and forced) */
+  int32_t reserved0;
+  double rel_res_recursive;/* ||r_last|| / ||b|| (recursively computed residual) */
+  double rel_res_true;     /* ||b - A x|| / ||b||, FP64 */
+  double time_ms;          /* device time of the persistent solver kernel (CUDA events
+                              recorded on the context's stream around its launch) */
+} pbcg_result;
+
+typedef struct pbcg_ctx pbcg_ctx;
+
+/* Fill *opt with defaults: FP64, max_it 10000, tol 1e-10, no replacement,
+ * timeout 2000 ms, no history, automatic launch shape.  opt: host, non-NULL. */
+pbcg_status pbicgstab_default_options(pbcg_options* opt);
+
+/* Create a solver context for A and M^{-1} (Algorithm 2's inputs other than b,
+ * x0).  Validates the matrix on the device (monotone row_ptr, columns in range
+ * and increasing, finite values, non-zero diagonal when M needs it), copies and
+ * converts it (FP32 copy in mixed mode, D^{-1}, the operator A D^{-1} used by the
+ * hot loop) and allocates the workspace.  out, A, M, opt: host, non-NULL.
+ * Errors: INVALID_ARG (bad arguments or matrix), OUT_OF_MEMORY, CUDA_ERROR. */
+pbcg_status pbicgstab_create(pbcg_ctx** out, const pbcg_matrix* A, const pbcg_precond* M,
+                             const pbcg_options* opt, void* stream);
+
+/* Replace the solve options (tolerance, iteration limit, replacement policy,
+ * history buffers, launch shape) of an existing context.  The precision cannot
+ * change.  ctx, opt: host, non-NULL. */
+pbcg_status pbicgstab_set_options(pbcg_ctx* ctx, const pbcg_options* opt);
+
+/* Solve A x = b with p-BiCGStab (Algorithm 2 with Eq. rr replacements per the
+ * options).  b: device, n doubles, read only.  x: device, n doubles, read as
+ * x0 and overwritten with the last iterate (the solution on PBCG_OK).  res: host
+ * or NULL; when non-NULL the call waits for the solve and fills it, otherwise it
+ * only enqueues the work.  The returned status is the solve's status when res is
+ * given, else PBCG_OK once the launch succeeded. */
+pbcg_status pbicgstab_solve(pbcg_ctx* ctx, const double* b, double* x, pbcg_result* res);
+
+/* Same as pbicgstab_solve with b and x in HOST memory (pinned or pageable): the
+ * host-to-device copy of b and x0, the solve and the device-to-host copy of x are
+ * enqueued on the context's stream and waited for.  res: host, non-NULL. */
+pbcg_status pbicgstab_solve_host(pbcg_ctx* ctx, const double* b_host, double* x_host,
+                                 pbcg_result* res);
+
+/* y = A x with the context's FP64 matrix (x, y: device, n doubles). */
+pbcg_status pbicgstab_spmv(pbcg_ctx* ctx, const double* x, double* y);
+
+/* *rel = ||b - A x|| / ||b|| in FP64 (b, x: device; rel: host).  Waits. */
+pbcg_status pbicgstab_true_residual(pbcg_ctx* ctx, const double* b, const double* x, double* rel);
+
+/* Release everything the context owns.  NULL is accepted. */
+pbcg_status pbicgstab_destroy(pbcg_ctx* ctx);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char* pbicgstab_last_error(void);
+
+/* Test hook for the fault-detection path: launches a cooperative grid whose
+ * blocks wait at a barrier for `extra_arrivals` more blocks than exist, so the
+ * wait can only end by its timeout.  Returns PBCG_OK when the kernel gave up
+ * after about timeout_ms and reported PBCG_TIMEOUT in *kernel_status (host).
+ * Nothing faults or hangs: every wait has an iteration limit. */
+pbcg_status pbicgstab_test_barrier_timeout(double timeout_ms, int32_t extra_arrivals,
+                                           int32_t* kernel_status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBICGSTAB_H */

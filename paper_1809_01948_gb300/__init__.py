@@ -1,0 +1,183 @@
+"""GB300 (sm_103a) p-BiCGStab: Python binding of libpbicgstab (include/pbicgstab.h).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  If the library is not
+built, importing works but every call raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import torch
+
+from . import _capi as capi
+from ._capi import Result, STATUS_NAMES  # noqa: F401
+
+__all__ = ["Solver", "PBCGError", "build", "STATUS_NAMES", "test_barrier_timeout"]
+
+
+class PBCGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    from ._build import build as _b
+    return _b(verbose=verbose, force=force)
+
+
+def _lib():
+    return capi.load()
+
+
+def _check(st: int, what: str):
+    if st != capi.PBCG_OK:
+        raise PBCGError(st, "%s: %s" % (what, capi.last_error()))
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+_PREC = {"none": capi.PREC_NONE, "jacobi": capi.PREC_JACOBI, "neumann": capi.PREC_NEUMANN}
+_PRECISION = {"fp64": capi.FP64, "mixed": capi.MIXED}
+
+
+class Solver:
+    """A p-BiCGStab solver context for one matrix (``pbicgstab_create``).
+
+    CSR: ``row_ptr`` (int32, n+1), ``col`` (int32, nnz), ``val`` (float64/float32, nnz).
+    DIA: ``offsets`` (ints, ascending, containing 0) and ``dia`` (ndiag x n values).
+    All tensors must be on the CUDA device; the library copies what it keeps.
+    """
+
+    def __init__(self, n: int, *, row_ptr=None, col=None, val=None, offsets: Sequence[int] = None,
+                 dia: torch.Tensor = None, precond: str = "jacobi", degree: int = 0,
+                 precision: str = "fp64", tol: float = 1e-10, max_it: int = 10000, rr_period: int = 0,
+                 rr_theta: float = 0.0, timeout_ms: float = 2000.0, grid_blocks: int = 0,
+                 block_threads: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        lib = _lib()
+        self.n = int(n)
+        self.stream = stream
+        m = capi.Matrix()
+        m.n = self.n
+        self._keep = []
+        if dia is not None:
+            if not (dia.is_cuda and dia.dim() == 2 and dia.shape[1] == self.n):
+                raise ValueError("dia must be a CUDA tensor of shape (ndiag, n)")
+            dia = dia.contiguous()
+            m.format = capi.FMT_DIA
+            m.val_dtype = capi.F64 if dia.dtype == torch.float64 else capi.F32
+            m.val = _ptr(dia)
+            offs = (C.c_int32 * len(offsets))(*[int(o) for o in offsets])
+            self._keep.append(offs)
+            m.ndiag = len(offsets)
+            m.offsets = C.cast(offs, C.c_void_p)
+            self._keep.append(dia)
+        else:
+            for t in (row_ptr, col, val):
+                if t is None or not t.is_cuda:
+                    raise ValueError("CSR arrays must be CUDA tensors")
+            row_ptr = row_ptr.to(torch.int32).contiguous()
+            col = col.to(torch.int32).contiguous()
+            val = val.contiguous()
+            m.format = capi.FMT_CSR
+            m.val_dtype = capi.F64 if val.dtype == torch.float64 else capi.F32
+            m.nnz = int(col.numel())
+            m.row_ptr, m.col, m.val = _ptr(row_ptr), _ptr(col), _ptr(val)
+            self._keep += [row_ptr, col, val]
+        p = capi.Precond(_PREC[precond], int(degree))
+        self.opt = capi.Options()
+        _check(lib.pbicgstab_default_options(C.byref(self.opt)), "default_options")
+        self.opt.precision = _PRECISION[precision]
+        self.opt.tol = tol
+        self.opt.max_it = max_it
+        self.opt.rr_period = rr_period
+        self.opt.rr_theta = rr_theta
+        self.opt.timeout_ms = timeout_ms
+        self.opt.grid_blocks = grid_blocks
+        self.opt.block_threads = block_threads
+        self.ctx = C.c_void_p()
+        _check(lib.pbicgstab_create(C.byref(self.ctx), C.byref(m), C.byref(p), C.byref(self.opt),
+                                    _stream_handle(stream)), "pbicgstab_create")
+        self._keep = []   # the library keeps its own copies
+
+    # -------------------------------------------------------------- options
+    def set_options(self, **kw):
+        hist_x = kw.pop("hist_x", None)
+        hist_scalars = kw.pop("hist_scalars", None)
+        for k, v in kw.items():
+            if k == "precision":
+                v = _PRECISION[v]
+            setattr(self.opt, k, v)
+        self.opt.hist_x = _ptr(hist_x) if hist_x is not None else None
+        self.opt.hist_scalars = _ptr(hist_scalars) if hist_scalars is not None else None
+        if hist_x is None:
+            self.opt.record_iterates = 0
+        if hist_scalars is None:
+            self.opt.hist_len = 0
+        _check(_lib().pbicgstab_set_options(self.ctx, C.byref(self.opt)), "pbicgstab_set_options")
+
+    # -------------------------------------------------------------- solve
+    def solve(self, b: torch.Tensor, x: Optional[torch.Tensor] = None, wait: bool = True,
+              raise_on_failure: bool = False):
+        """x <- solution of A x = b (x is the initial guess, default 0).  Returns (x, Result|None)."""
+        if not (b.is_cuda and b.dtype == torch.float64 and b.numel() == self.n and b.is_contiguous()):
+            raise ValueError("b must be a contiguous CUDA float64 vector of length n")
+        if x is None:
+            x = torch.zeros_like(b)
+        elif not (x.is_cuda and x.dtype == torch.float64 and x.numel() == self.n and x.is_contiguous()):
+            raise ValueError("x must be a contiguous CUDA float64 vector of length n")
+        res = capi.Result() if wait else None
+        st = _lib().pbicgstab_solve(self.ctx, _ptr(b), _ptr(x), C.byref(res) if wait else None)
+        if st in (capi.PBCG_INVALID_ARG, capi.PBCG_CUDA_ERROR, capi.PBCG_OUT_OF_MEMORY, capi.PBCG_TIMEOUT) or (
+                raise_on_failure and st != capi.PBCG_OK):
+            raise PBCGError(st, capi.last_error())
+        return x, res
+
+    def solve_host(self, b_host, x_host):
+        """End-to-end solve with host (numpy float64) buffers: copies in, solve, copy out."""
+        import numpy as np
+        b_host = np.ascontiguousarray(b_host, dtype=np.float64)
+        if x_host.dtype != np.float64 or not x_host.flags.c_contiguous:
+            raise ValueError("x_host must be a contiguous float64 array")
+        res = capi.Result()
+        st = _lib().pbicgstab_solve_host(self.ctx, b_host.ctypes.data_as(C.c_void_p),
+                                         x_host.ctypes.data_as(C.c_void_p), C.byref(res))
+        if st in (capi.PBCG_INVALID_ARG, capi.PBCG_CUDA_ERROR, capi.PBCG_OUT_OF_MEMORY, capi.PBCG_TIMEOUT):
+            raise PBCGError(st, capi.last_error())
+        return x_host, res
+
+    def spmv(self, x: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
+        y = torch.empty_like(x) if y is None else y
+        _check(_lib().pbicgstab_spmv(self.ctx, _ptr(x), _ptr(y)), "pbicgstab_spmv")
+        return y
+
+    def true_residual(self, b: torch.Tensor, x: torch.Tensor) -> float:
+        out = C.c_double()
+        _check(_lib().pbicgstab_true_residual(self.ctx, _ptr(b), _ptr(x), C.byref(out)), "true_residual")
+        return out.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _lib().pbicgstab_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def test_barrier_timeout(timeout_ms: float = 200.0, extra_arrivals: int = 1) -> str:
+    st = C.c_int32(-1)
+    _check(_lib().pbicgstab_test_barrier_timeout(timeout_ms, extra_arrivals, C.byref(st)), "barrier test")
+    return STATUS_NAMES.get(st.value, str(st.value))

@@ -1,0 +1,646 @@
+// Host side of libpbicgstab: argument validation, matrix preparation, workspace,
+// cooperative launch of the persistent solver, FP64 true residual.  C ABI in
+// include/pbicgstab.h.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/pbicgstab.h"
+#include "capi_internal.h"
+#include "solver.cuh"
+
+using namespace pbcg;
+
+namespace pbcg {
+thread_local std::string g_last_error;
+
+pbcg_status set_error(pbcg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+pbcg_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PBCG_OK;
+  cudaGetLastError();  // clear sticky-free errors
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(PBCG_OUT_OF_MEMORY, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(PBCG_CUDA_ERROR, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+}  // namespace pbcg
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    pbcg_status st__ = cuda_status((call), (what));      \
+    if (st__ != PBCG_OK) return st__;                    \
+  } while (0)
+
+// ----------------------------------------------------------------------------
+// preparation kernels
+// ----------------------------------------------------------------------------
+// flags: bit0 row_ptr not monotone / wrong ends, bit1 column out of range or not
+// increasing, bit2 non-finite value, bit3 missing or zero diagonal (when required)
+__global__ void validate_csr_kernel(int n, long long nnz, const int* row_ptr, const int* col,
+                                    const void* val, int f32, int need_diag, int* flags, double* diag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int f = 0;
+  const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
+  if (i == 0 && e0 != 0) f |= 1;
+  if (i == n - 1 && (long long)e1 != nnz) f |= 1;
+  if (e1 < e0 || e0 < 0 || (long long)e1 > nnz) {
+    atomicOr(flags, f | 1);
+    return;
+  }
+  double dg = 0.0;
+  int prev = -1;
+  for (int e = e0; e < e1; ++e) {
+    const int c = col[e];
+    if (c < 0 || c >= n || c <= prev) f |= 2;
+    prev = c;
+    const double v = f32 ? (double)((const float*)val)[e] : ((const double*)val)[e];
+    if (!isfinite(v)) f |= 4;
+    if (c == i) dg = v;
+  }
+  if (need_diag && dg == 0.0) f |= 8;
+  diag[i] = dg;
+  if (f) atomicOr(flags, f);
+}
+
+__global__ void validate_dia_kernel(int n, int ndiag, MatView<double> offs_only, const void* val, int f32,
+                                    int need_diag, int* flags, double* diag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int f = 0;
+  double dg = 0.0;
+  for (int d = 0; d < ndiag; ++d) {
+    const size_t idx = (size_t)d * n + i;
+    const double v = f32 ? (double)((const float*)val)[idx] : ((const double*)val)[idx];
+    const int j = i + offs_only.off[d];
+    if (j < 0 || j >= n) continue;
+    if (!isfinite(v)) f |= 4;
+    if (offs_only.off[d] == 0) dg = v;
+  }
+  if (need_diag && dg == 0.0) f |= 8;
+  diag[i] = dg;
+  if (f) atomicOr(flags, f);
+}
+
+__global__ void to_f64_kernel(long long m, const void* src, int f32, double* dst) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  dst[i] = f32 ? (double)((const float*)src)[i] : ((const double*)src)[i];
+}
+
+template <typename T>
+__global__ void cast_kernel(long long m, const double* src, T* dst) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < m) dst[i] = T(src[i]);
+}
+
+__global__ void dinv_kernel(int n, const double* diag, double* dinv64) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dinv64[i] = 1.0 / diag[i];
+}
+
+// A D^{-1}: column j scaled by d_inv[j], rounded once to T.
+template <typename T>
+__global__ void fold_csr_kernel(int n, const int* row_ptr, const int* col, const double* val,
+                                const double* dinv, T* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) out[e] = T(val[e] * dinv[col[e]]);
+}
+
+// DIA fold: the main diagonal of A D^{-1} is exactly 1 and is not stored
+// (MatView::unit_diag); the other diagonals are scaled by d_inv of their column.
+template <typename T>
+__global__ void fold_dia_kernel(int n, MatView<double> src, const double* dinv, T* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int dd = 0;
+  for (int d = 0; d < src.ndiag; ++d) {
+    if (src.off[d] == 0) continue;
+    const int j = i + src.off[d];
+    const double v = src.val[(size_t)d * n + i];
+    out[(size_t)dd * n + i] = (j >= 0 && j < n) ? T(v * dinv[j]) : T(0);
+    ++dd;
+  }
+}
+
+// FP64 ||b - A x||^2 and ||b||^2, block partials then one fixed-order final sum.
+__global__ void true_res_partial_kernel(MatView<double> A, const double* b, const double* x, double* part) {
+  __shared__ double smem[32 * kMaxDots];
+  double v[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+    const double r = b[i] - row_dot<double>(A, x, i);
+    v[0] = fma(r, r, v[0]);
+    v[1] = fma(b[i], b[i], v[1]);
+  }
+  block_publish<2>(v, smem, part);
+}
+
+__global__ void true_res_final_kernel(const double* part, int nparts, double* out) {
+  __shared__ double smem[32 * kMaxDots];
+  double v[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+    v[0] += part[b * kMaxDots + 0];
+    v[1] += part[b * kMaxDots + 1];
+  }
+  block_sum<2>(v, smem);
+  if (threadIdx.x == 0) out[0] = v[1] > 0.0 ? sqrt(v[0]) / sqrt(v[1]) : sqrt(v[0]);
+}
+
+__global__ void spmv_kernel(MatView<double> A, const double* x, double* y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x)
+    y[i] = row_dot<double>(A, x, i);
+}
+
+// Test hook: every block waits for gridDim.x + extra arrivals, which never come.
+__global__ void barrier_timeout_kernel(unsigned* counter, int* err, int extra, unsigned long long timeout_ns) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    red_release_add(counter, 1u);
+    const unsigned target = gridDim.x + (unsigned)extra;
+    const unsigned long long t0 = global_ns();
+    unsigned spins = 0;
+    while (ld_acquire_u32(counter) < target) {
+      if ((++spins & 63u) == 0 && global_ns() - t0 > timeout_ns) {
+        atomicCAS(err, 0, (int)kTimeout);
+        break;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------
+// context
+// ----------------------------------------------------------------------------
+struct DevState {
+  DevResult res;
+  unsigned bar;
+  int err;
+  double true_rel;
+  int flags;
+  int reserved;
+};
+
+struct pbcg_ctx {
+  int n = 0;
+  long long nnz = 0;
+  int fmt = 0;
+  int precision = 0;
+  int prec_kind = 0;
+  int degree = 0;
+  cudaStream_t stream = nullptr;
+  pbcg_options opt{};
+  // matrix (device, owned)
+  int* row_ptr = nullptr;
+  int* col = nullptr;
+  double* val64 = nullptr;   // FP64 values (CSR nnz, DIA ndiag*n)
+  void* valAt = nullptr;     // hot operator values in T
+  void* valAu = nullptr;     // A in T (mixed: FP32 copy; FP64: aliases val64)
+  double* diag64 = nullptr;
+  double* dinv64 = nullptr;
+  void* dinvT = nullptr;
+  int ndiag = 0;
+  int offsets[kMaxDiag] = {0};
+  int ndiag_t = 0;           // diagonals stored in valAt (DIA fold drops the main one)
+  int offsets_t[kMaxDiag] = {0};
+  int at_unit_diag = 0;
+  // vectors + reductions
+  void* vecs = nullptr;
+  int nvec = 15;
+  double* part = nullptr;
+  int max_blocks = 0;
+  DevState* dstate = nullptr;
+  DevState* hstate = nullptr;  // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+static size_t elem_size(int precision) { return precision == PBCG_MIXED ? sizeof(float) : sizeof(double); }
+
+template <typename V>
+static MatView<V> make_view(const pbcg_ctx* c, const V* val, bool hot) {
+  MatView<V> m;
+  memset(&m, 0, sizeof m);
+  m.fmt = c->fmt;
+  m.n = c->n;
+  m.row_ptr = c->row_ptr;
+  m.col = c->col;
+  m.val = val;
+  if (c->fmt == PBCG_FMT_DIA) {
+    if (hot) {
+      m.ndiag = c->ndiag_t;
+      m.unit_diag = c->at_unit_diag;
+      for (int d = 0; d < c->ndiag_t; ++d) m.off[d] = c->offsets_t[d];
+    } else {
+      m.ndiag = c->ndiag;
+      for (int d = 0; d < c->ndiag; ++d) m.off[d] = c->offsets[d];
+    }
+  }
+  return m;
+}
+
+MatView<double> pbcg_view64(const pbcg_ctx* c) { return make_view<double>(c, c->val64, false); }
+cudaStream_t pbcg_stream(const pbcg_ctx* c) { return c->stream; }
+int pbcg_n(const pbcg_ctx* c) { return c->n; }
+
+static void free_ctx(pbcg_ctx* c) {
+  if (!c) return;
+  if (c->valAu && c->valAu != (void*)c->val64) cudaFree(c->valAu);
+  void* ptrs[] = {c->row_ptr, c->col, c->val64, c->valAt, c->diag64, c->dinv64, c->dinvT,
+                  c->vecs, c->part, c->dstate};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->hstate) cudaFreeHost(c->hstate);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+static pbcg_status check_options(const pbcg_options* o, long long n) {
+  if (o->precision != PBCG_FP64 && o->precision != PBCG_MIXED)
+    return set_error(PBCG_INVALID_ARG, "options.precision must be PBCG_FP64 or PBCG_MIXED");
+  if (o->max_it < 0) return set_error(PBCG_INVALID_ARG, "options.max_it must be >= 0");
+  if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return set_error(PBCG_INVALID_ARG, "options.tol must be finite and >= 0");
+  if (o->rr_period < 0) return set_error(PBCG_INVALID_ARG, "options.rr_period must be >= 0");
+  if (o->rr_auto != 0) return set_error(PBCG_INVALID_ARG, "options.rr_auto is reserved and must be 0");
+  if (!(o->rr_theta >= 0.0 && o->rr_theta < 1.0)) return set_error(PBCG_INVALID_ARG, "options.rr_theta must be in [0, 1)");
+  if (o->record_iterates < 0 || (o->record_iterates > 0 && !o->hist_x))
+    return set_error(PBCG_INVALID_ARG, "options.record_iterates > 0 needs hist_x");
+  if (o->hist_len < 0 || (o->hist_len > 0 && !o->hist_scalars))
+    return set_error(PBCG_INVALID_ARG, "options.hist_len > 0 needs hist_scalars");
+  if (o->block_threads != 0 && (o->block_threads < 32 || o->block_threads > kMaxThreads || o->block_threads % 32))
+    return set_error(PBCG_INVALID_ARG, "options.block_threads must be 0 or a multiple of 32 in [32, 1024]");
+  if (o->grid_blocks < 0) return set_error(PBCG_INVALID_ARG, "options.grid_blocks must be >= 0");
+  (void)n;
+  return PBCG_OK;
+}
+
+template <typename T>
+static const void* kernel_ptr() { return (const void*)pbicgstab_kernel<T>; }
+
+static int kernel_threads(const pbcg_ctx* c) {
+  return c->opt.block_threads ? c->opt.block_threads : 512;
+}
+
+static pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads) {
+  const int nt = kernel_threads(c);
+  int per_sm = 0;
+  const void* k = c->precision == PBCG_MIXED ? kernel_ptr<float>() : kernel_ptr<double>();
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, 0), "occupancy query");
+  const int sms = sm_count();
+  const int max_coresident = per_sm * sms;
+  if (max_coresident <= 0) return set_error(PBCG_INVALID_ARG, "kernel cannot be resident with %d threads per block", nt);
+  int g = c->opt.grid_blocks;
+  if (g == 0) {
+    // about 4 rows per thread at most 2 blocks per SM; tiny systems use fewer blocks
+    const long long want = (c->n + (long long)nt * 4 - 1) / ((long long)nt * 4);
+    g = (int)std::min<long long>(std::max<long long>(1, want), (long long)std::min(max_coresident, 2 * sms));
+  }
+  if (g > max_coresident)
+    return set_error(PBCG_INVALID_ARG, "grid_blocks %d exceeds the %d co-resident blocks", g, max_coresident);
+  if (g > c->max_blocks) return set_error(PBCG_INVALID_ARG, "grid_blocks %d exceeds workspace (%d)", g, c->max_blocks);
+  *grid = g;
+  *threads = nt;
+  return PBCG_OK;
+}
+
+extern "C" pbcg_status pbicgstab_default_options(pbcg_options* o) {
+  if (!o) return set_error(PBCG_INVALID_ARG, "opt is NULL");
+  memset(o, 0, sizeof *o);
+  o->precision = PBCG_FP64;
+  o->max_it = 10000;
+  o->tol = 1e-10;
+  o->timeout_ms = 2000.0;
+  return PBCG_OK;
+}
+
+extern "C" const char* pbicgstab_last_error(void) { return g_last_error.c_str(); }
+
+static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
+  const int n = c->n;
+  const int nb = (n + 255) / 256;
+  const int f32 = A->val_dtype == PBCG_F32;
+  const bool need_diag = c->prec_kind != PBCG_PREC_NONE;
+  int* dflags = &c->dstate->flags;
+  CK(cudaMemsetAsync(dflags, 0, sizeof(int), c->stream), "memset");
+  CK(cudaMalloc(&c->diag64, sizeof(double) * n), "cudaMalloc diag");
+  long long nval;
+  if (c->fmt == PBCG_FMT_CSR) {
+    nval = c->nnz;
+    CK(cudaMalloc(&c->row_ptr, sizeof(int) * (n + 1)), "cudaMalloc row_ptr");
+    CK(cudaMalloc(&c->col, sizeof(int) * std::max<long long>(1, c->nnz)), "cudaMalloc col");
+    CK(cudaMemcpyAsync(c->row_ptr, A->row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, c->stream), "copy row_ptr");
+    if (c->nnz)
+      CK(cudaMemcpyAsync(c->col, A->col, sizeof(int) * c->nnz, cudaMemcpyDeviceToDevice, c->stream), "copy col");
+    validate_csr_kernel<<<nb, 256, 0, c->stream>>>(n, c->nnz, c->row_ptr, c->col, A->val, f32, need_diag, dflags, c->diag64);
+  } else {
+    nval = (long long)c->ndiag * n;
+    MatView<double> offs;
+    memset(&offs, 0, sizeof offs);
+    for (int d = 0; d < c->ndiag; ++d) offs.off[d] = c->offsets[d];
+    validate_dia_kernel<<<nb, 256, 0, c->stream>>>(n, c->ndiag, offs, A->val, f32, need_diag, dflags, c->diag64);
+  }
+  CK(cudaGetLastError(), "validate kernel");
+  CK(cudaMalloc(&c->val64, sizeof(double) * std::max<long long>(1, nval)), "cudaMalloc values");
+  const long long nbv = (nval + 255) / 256;
+  if (nval) to_f64_kernel<<<(unsigned)nbv, 256, 0, c->stream>>>(nval, A->val, f32, c->val64);
+  CK(cudaGetLastError(), "convert kernel");
+  int hflags = 0;
+  CK(cudaMemcpyAsync(&hflags, dflags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy flags");
+  CK(cudaStreamSynchronize(c->stream), "validate");
+  if (hflags & 1) return set_error(PBCG_INVALID_ARG, "CSR row_ptr is not monotone from 0 to nnz");
+  if (hflags & 2) return set_error(PBCG_INVALID_ARG, "CSR column index out of range or not strictly increasing in a row");
+  if (hflags & 4) return set_error(PBCG_INVALID_ARG, "matrix has a non-finite value");
+  if (hflags & 8) return set_error(PBCG_INVALID_ARG, "the preconditioner needs a non-zero diagonal entry in every row");
+
+  const size_t es = elem_size(c->precision);
+  const bool mixed = c->precision == PBCG_MIXED;
+  if (need_diag) {
+    CK(cudaMalloc(&c->dinv64, sizeof(double) * n), "cudaMalloc dinv");
+    dinv_kernel<<<nb, 256, 0, c->stream>>>(n, c->diag64, c->dinv64);
+    if (mixed) {
+      CK(cudaMalloc(&c->dinvT, sizeof(float) * n), "cudaMalloc dinv32");
+      cast_kernel<float><<<nb, 256, 0, c->stream>>>(n, c->dinv64, (float*)c->dinvT);
+    } else {
+      c->dinvT = nullptr;
+    }
+  }
+  // unfolded A in T
+  if (mixed) {
+    CK(cudaMalloc(&c->valAu, sizeof(float) * std::max<long long>(1, nval)), "cudaMalloc A32");
+    if (nval) cast_kernel<float><<<(unsigned)nbv, 256, 0, c->stream>>>(nval, c->val64, (float*)c->valAu);
+  } else {
+    c->valAu = c->val64;
+  }
+  // hot operator: A D^{-1} with a preconditioner, A otherwise
+  if (!need_diag) {
+    c->valAt = nullptr;
+    c->ndiag_t = c->ndiag;
+    for (int d = 0; d < c->ndiag; ++d) c->offsets_t[d] = c->offsets[d];
+    c->at_unit_diag = 0;
+  } else if (c->fmt == PBCG_FMT_CSR) {
+    CK(cudaMalloc(&c->valAt, es * std::max<long long>(1, nval)), "cudaMalloc A D^-1");
+    if (mixed) fold_csr_kernel<float><<<nb, 256, 0, c->stream>>>(n, c->row_ptr, c->col, c->val64, c->dinv64, (float*)c->valAt);
+    else fold_csr_kernel<double><<<nb, 256, 0, c->stream>>>(n, c->row_ptr, c->col, c->val64, c->dinv64, (double*)c->valAt);
+  } else {
+    int dd = 0;
+    for (int d = 0; d < c->ndiag; ++d)
+      if (c->offsets[d] != 0) c->offsets_t[dd++] = c->offsets[d];
+    c->ndiag_t = dd;
+    c->at_unit_diag = 1;
+    CK(cudaMalloc(&c->valAt, es * std::max<long long>(1, (long long)dd * n)), "cudaMalloc A D^-1");
+    MatView<double> src = make_view<double>(c, c->val64, false);
+    if (mixed) fold_dia_kernel<float><<<nb, 256, 0, c->stream>>>(n, src, c->dinv64, (float*)c->valAt);
+    else fold_dia_kernel<double><<<nb, 256, 0, c->stream>>>(n, src, c->dinv64, (double*)c->valAt);
+  }
+  CK(cudaGetLastError(), "prepare kernels");
+  return PBCG_OK;
+}
+
+extern "C" pbcg_status pbicgstab_create(pbcg_ctx** out, const pbcg_matrix* A, const pbcg_precond* M,
+                                        const pbcg_options* opt, void* stream) {
+  if (!out || !A || !M || !opt) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_create");
+  *out = nullptr;
+  if (A->n <= 0 || A->n >= 2147483647LL) return set_error(PBCG_INVALID_ARG, "n must be in [1, 2^31-2]");
+  if (A->format != PBCG_FMT_CSR && A->format != PBCG_FMT_DIA) return set_error(PBCG_INVALID_ARG, "unknown matrix format");
+  if (A->val_dtype != PBCG_F64 && A->val_dtype != PBCG_F32) return set_error(PBCG_INVALID_ARG, "unknown value dtype");
+  if (!A->val) return set_error(PBCG_INVALID_ARG, "matrix values are NULL");
+  if (A->format == PBCG_FMT_CSR) {
+    if (!A->row_ptr || (A->nnz > 0 && !A->col)) return set_error(PBCG_INVALID_ARG, "CSR arrays are NULL");
+    if (A->nnz < 0 || A->nnz >= 2147483647LL) return set_error(PBCG_INVALID_ARG, "nnz must be in [0, 2^31-2]");
+  } else {
+    if (A->ndiag < 1 || A->ndiag > kMaxDiag || !A->offsets)
+      return set_error(PBCG_INVALID_ARG, "DIA needs 1..%d diagonals and host offsets", kMaxDiag);
+    bool has0 = false;
+    for (int d = 0; d < A->ndiag; ++d) {
+      if (d > 0 && A->offsets[d] <= A->offsets[d - 1]) return set_error(PBCG_INVALID_ARG, "DIA offsets must increase");
+      if (A->offsets[d] <= -A->n || A->offsets[d] >= A->n) return set_error(PBCG_INVALID_ARG, "DIA offset out of range");
+      has0 |= A->offsets[d] == 0;
+    }
+    if (!has0) return set_error(PBCG_INVALID_ARG, "DIA offsets must contain the main diagonal 0");
+  }
+  if (M->kind < PBCG_PREC_NONE || M->kind > PBCG_PREC_NEUMANN) return set_error(PBCG_INVALID_ARG, "unknown preconditioner");
+  if (M->kind == PBCG_PREC_NEUMANN && (M->degree < 1 || M->degree > 8))
+    return set_error(PBCG_INVALID_ARG, "Neumann degree must be in [1, 8]");
+  pbcg_status st = check_options(opt, A->n);
+  if (st != PBCG_OK) return st;
+
+  pbcg_ctx* c = new (std::nothrow) pbcg_ctx();
+  if (!c) return set_error(PBCG_OUT_OF_MEMORY, "host allocation failed");
+  c->n = (int)A->n;
+  c->nnz = A->format == PBCG_FMT_CSR ? A->nnz : 0;
+  c->fmt = A->format;
+  c->precision = opt->precision;
+  c->prec_kind = M->kind;
+  c->degree = M->kind == PBCG_PREC_NEUMANN ? M->degree : 0;
+  c->stream = (cudaStream_t)stream;
+  c->opt = *opt;
+  c->ndiag = A->format == PBCG_FMT_DIA ? A->ndiag : 0;
+  for (int d = 0; d < c->ndiag; ++d) c->offsets[d] = A->offsets[d];
+#define CKC(call, what)                                  \
+  do {                                                   \
+    pbcg_status s__ = cuda_status((call), (what));       \
+    if (s__ != PBCG_OK) { free_ctx(c); return s__; }     \
+  } while (0)
+  CKC(cudaMalloc(&c->dstate, sizeof(DevState)), "cudaMalloc state");
+  CKC(cudaMallocHost(&c->hstate, sizeof(DevState)), "cudaMallocHost state");
+  CKC(cudaEventCreate(&c->ev0), "event");
+  CKC(cudaEventCreate(&c->ev1), "event");
+  st = prepare_matrix(c, A);
+  if (st != PBCG_OK) { free_ctx(c); return st; }
+  const size_t es = elem_size(c->precision);
+  CKC(cudaMalloc(&c->vecs, es * (size_t)c->n * c->nvec), "cudaMalloc workspace");
+  c->max_blocks = 4 * kMaxThreads;  // generous: any co-resident grid fits
+  CKC(cudaMalloc(&c->part, sizeof(double) * 3 * kMaxDots * (size_t)c->max_blocks), "cudaMalloc partials");
+  CKC(cudaStreamSynchronize(c->stream), "create");
+  *out = c;
+  return PBCG_OK;
+#undef CKC
+}
+
+extern "C" pbcg_status pbicgstab_set_options(pbcg_ctx* c, const pbcg_options* opt) {
+  if (!c || !opt) return set_error(PBCG_INVALID_ARG, "NULL argument");
+  pbcg_status st = check_options(opt, c->n);
+  if (st != PBCG_OK) return st;
+  if (opt->precision != c->precision) return set_error(PBCG_INVALID_ARG, "precision cannot change after create");
+  c->opt = *opt;
+  return PBCG_OK;
+}
+
+extern "C" pbcg_status pbicgstab_destroy(pbcg_ctx* c) {
+  if (!c) return PBCG_OK;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+  return PBCG_OK;
+}
+
+template <typename T>
+static SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int grid) {
+  SolverParams<T> p;
+  memset(&p, 0, sizeof p);
+  const int n = c->n;
+  p.n = n;
+  p.chunk = (n + grid - 1) / grid;
+  const T* at = c->valAt ? (const T*)c->valAt : (const T*)c->valAu;
+  p.At = make_view<T>(c, at, c->valAt != nullptr);
+  if (!c->valAt && c->fmt == PBCG_FMT_DIA) p.At = make_view<T>(c, at, false);
+  p.Au = make_view<T>(c, (const T*)c->valAu, false);
+  p.A64 = make_view<double>(c, c->val64, false);
+  p.dinv = c->prec_kind == PBCG_PREC_NONE ? nullptr
+           : (std::is_same<T, float>::value ? (const T*)c->dinvT : (const T*)c->dinv64);
+  p.prec = c->prec_kind;
+  p.degree = c->degree;
+  p.b = b;
+  p.x = x;
+  T* v = (T*)c->vecs;
+  T** slots[] = {&p.r, &p.rh, &p.k, &p.w, &p.g, &p.s, &p.l, &p.z, &p.v, &p.t, &p.nb, &p.m, &p.nn, &p.tmpa, &p.tmpb};
+  for (int j = 0; j < 15; ++j) *slots[j] = v + (size_t)j * n;
+  p.part = c->part;
+  p.bar = &c->dstate->bar;
+  p.err = &c->dstate->err;
+  p.res = &c->dstate->res;
+  p.hist_x = c->opt.hist_x;
+  p.K = c->opt.record_iterates;
+  p.hist_s = c->opt.hist_scalars;
+  p.hist_len = c->opt.hist_len;
+  p.tol = c->opt.tol;
+  p.max_it = c->opt.max_it;
+  p.rr_period = c->opt.rr_period;
+  p.rr_theta = c->opt.rr_theta;
+  const double tms = c->opt.timeout_ms > 0 ? c->opt.timeout_ms : 2000.0;
+  p.timeout_ns = (unsigned long long)(tms * 1e6);
+  return p;
+}
+
+static pbcg_status enqueue_true_residual(pbcg_ctx* c, const double* b, const double* x, double* out_dev) {
+  const int sms = sm_count();
+  const int nb = std::min(c->max_blocks, std::max(1, std::min(2 * sms, (c->n + 255) / 256)));
+  true_res_partial_kernel<<<nb, 256, 0, c->stream>>>(pbcg_view64(c), b, x, c->part);
+  true_res_final_kernel<<<1, 256, 0, c->stream>>>(c->part, nb, out_dev);
+  CK(cudaGetLastError(), "true residual kernels");
+  return PBCG_OK;
+}
+
+static pbcg_status enqueue_solve(pbcg_ctx* c, const double* b, double* x) {
+  int grid = 0, threads = 0;
+  pbcg_status st = launch_shape(c, &grid, &threads);
+  if (st != PBCG_OK) return st;
+  CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->stream), "memset state");
+  CK(cudaEventRecord(c->ev0, c->stream), "event record");
+  if (c->precision == PBCG_MIXED) {
+    SolverParams<float> p = make_params<float>(c, b, x, grid);
+    void* args[] = {&p};
+    CK(cudaLaunchCooperativeKernel(kernel_ptr<float>(), grid, threads, args, 0, c->stream), "cooperative launch");
+  } else {
+    SolverParams<double> p = make_params<double>(c, b, x, grid);
+    void* args[] = {&p};
+    CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(), grid, threads, args, 0, c->stream), "cooperative launch");
+  }
+  CK(cudaEventRecord(c->ev1, c->stream), "event record");
+  return enqueue_true_residual(c, b, x, &c->dstate->true_rel);
+}
+
+static pbcg_status collect(pbcg_ctx* c, pbcg_result* res) {
+  CK(cudaMemcpyAsync(c->hstate, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "copy state");
+  CK(cudaStreamSynchronize(c->stream), "solve");
+  const DevState& h = *c->hstate;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  memset(res, 0, sizeof *res);
+  res->status = h.err ? PBCG_TIMEOUT : h.res.status;
+  res->iterations = h.res.iterations;
+  res->n_replacements = h.res.nrep;
+  res->rel_res_recursive = h.res.rn_rel;
+  res->rel_res_true = h.true_rel;
+  res->time_ms = ms;
+  if (res->status == PBCG_TIMEOUT) return set_error(PBCG_TIMEOUT, "a grid-wide wait exceeded timeout_ms");
+  return (pbcg_status)res->status;
+}
+
+extern "C" pbcg_status pbicgstab_solve(pbcg_ctx* c, const double* b, double* x, pbcg_result* res) {
+  if (!c || !b || !x) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_solve");
+  pbcg_status st = enqueue_solve(c, b, x);
+  if (st != PBCG_OK) return st;
+  if (!res) return PBCG_OK;
+  return collect(c, res);
+}
+
+extern "C" pbcg_status pbicgstab_solve_host(pbcg_ctx* c, const double* b_host, double* x_host, pbcg_result* res) {
+  if (!c || !b_host || !x_host || !res) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_solve_host");
+  // b and x live in the spare tail of the workspace-sized staging buffers below
+  double* db = nullptr;
+  double* dx = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)c->n;
+  CK(cudaMallocAsync((void**)&db, bytes, c->stream), "cudaMallocAsync b");
+  CK(cudaMallocAsync((void**)&dx, bytes, c->stream), "cudaMallocAsync x");
+  CK(cudaMemcpyAsync(db, b_host, bytes, cudaMemcpyHostToDevice, c->stream), "copy b");
+  CK(cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, c->stream), "copy x0");
+  pbcg_status st = enqueue_solve(c, db, dx);
+  if (st == PBCG_OK) {
+    CK(cudaMemcpyAsync(x_host, dx, bytes, cudaMemcpyDeviceToHost, c->stream), "copy x");
+    st = collect(c, res);
+  }
+  cudaFreeAsync(db, c->stream);
+  cudaFreeAsync(dx, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return st;
+}
+
+extern "C" pbcg_status pbicgstab_spmv(pbcg_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_spmv");
+  const int nb = std::max(1, std::min(4 * sm_count(), (c->n + 255) / 256));
+  spmv_kernel<<<nb, 256, 0, c->stream>>>(pbcg_view64(c), x, y);
+  CK(cudaGetLastError(), "spmv kernel");
+  return PBCG_OK;
+}
+
+extern "C" pbcg_status pbicgstab_true_residual(pbcg_ctx* c, const double* b, const double* x, double* rel) {
+  if (!c || !b || !x || !rel) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_true_residual");
+  pbcg_status st = enqueue_true_residual(c, b, x, &c->dstate->true_rel);
+  if (st != PBCG_OK) return st;
+  CK(cudaMemcpyAsync(rel, &c->dstate->true_rel, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy");
+  CK(cudaStreamSynchronize(c->stream), "true residual");
+  return PBCG_OK;
+}
+
+extern "C" pbcg_status pbicgstab_test_barrier_timeout(double timeout_ms, int32_t extra, int32_t* kernel_status) {
+  if (!kernel_status || extra < 1 || !(timeout_ms > 0 && timeout_ms <= 10000))
+    return set_error(PBCG_INVALID_ARG, "need extra >= 1, 0 < timeout_ms <= 10000 and a status pointer");
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  CK(cudaMalloc(&bar, sizeof(unsigned)), "cudaMalloc");
+  CK(cudaMalloc(&err, sizeof(int)), "cudaMalloc");
+  CK(cudaMemset(bar, 0, sizeof(unsigned)), "memset");
+  CK(cudaMemset(err, 0, sizeof(int)), "memset");
+  const int grid = sm_count();
+  unsigned long long tns = (unsigned long long)(timeout_ms * 1e6);
+  int ex = extra;
+  void* args[] = {&bar, &err, &ex, &tns};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)barrier_timeout_kernel, grid, 64, args, 0, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(bar);
+  cudaFree(err);
+  CK(e, "barrier timeout kernel");
+  *kernel_status = h ? PBCG_TIMEOUT : PBCG_OK;
+  return PBCG_OK;
+}

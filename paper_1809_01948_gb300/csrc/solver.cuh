@@ -1,0 +1,377 @@
+// Persistent, cooperatively launched p-BiCGStab kernel (Algorithm 2 of arXiv
+// 1809.01948 with the residual replacement step of Eq. (rr)).
+//
+// One launch runs the whole solve.  Rows are split into one contiguous chunk per
+// block.  Each iteration is two fused passes separated by grid barriers; each pass
+// is an SPMV fused with the AXPY recurrences and the partial dot products of one
+// global reduction phase, so the paper's "overlap GLRED with SPMV + PREC" becomes:
+// the reduction completes at the barrier the next SPMV needs anyway.
+//
+//   pass A (lines 5-12 + 23 of iteration i-1): t_i = A m_i, then g, s, l, z, q, u, y
+//          and partials of (q,y), (y,y)
+//   pass B (lines 13-21): v_i = A n_i, omega_i, then x, r, k, w (q, u, y recomputed
+//          bit-identically instead of stored) and partials of (r0,r_{i+1}),
+//          (r0,w_{i+1}), (r0,s_i), (r0,z_i), (r_{i+1},r_{i+1})
+//
+// Jacobi / no preconditioner: m = D^{-1} w and n = D^{-1} z are formed on the fly and
+// the SPMVs use the folded operator A D^{-1} (t = A D^{-1} w = A m), so each
+// iteration has exactly two grid barriers.  Neumann(d): m and n are stored and each
+// M^{-1} application adds d barrier-separated Jacobi-sweep passes.
+//
+// Every block computes the scalars alpha, beta, omega from the same partials in the
+// same order, so all blocks take identical control-flow decisions without any
+// extra synchronisation.
+#pragma once
+#include "common.cuh"
+
+namespace pbcg {
+
+struct DevResult {
+  int status;
+  int iterations;
+  int nrep;
+  int reserved;
+  double rn_rel;   // ||r_last|| / ||b||
+  double bnorm;
+  double rn0;
+  double true_rel; // set when the in-kernel true residual was evaluated (else -1)
+};
+
+template <typename T>
+struct SolverParams {
+  int n, chunk;
+  MatView<T> At;        // hot operator: A D^{-1} (Jacobi, and Neumann's first sweep) or A (none)
+  MatView<T> Au;        // A in the vector precision (Neumann sweeps, t = A m, v = A n)
+  MatView<double> A64;  // A in FP64: initial and replacement residuals
+  const T* dinv;        // D^{-1} (nullptr without preconditioner)
+  int prec;             // 0 none, 1 Jacobi, 2 Neumann
+  int degree;
+  const double* b;
+  double* x;
+  T *r, *rh, *k, *w, *g, *s, *l, *z, *v, *t, *nb, *m, *nn, *tmpa, *tmpb;
+  double* part;         // 3 partial sets of gridDim.x * kMaxDots doubles
+  unsigned* bar;
+  int* err;
+  DevResult* res;
+  double* hist_x;
+  int K;
+  double* hist_s;
+  int hist_len;
+  double tol;
+  int max_it;
+  int rr_period;
+  double rr_theta;
+  unsigned long long timeout_ns;
+};
+
+template <typename T>
+__device__ __forceinline__ T minv_local(const SolverParams<T>& p, T v, int i) {
+  return p.prec == 1 ? T(__ldg(p.dinv + i) * v) : v;
+}
+
+// Neumann polynomial M^{-1} src = sum_{j<=d} (I - D^{-1}A)^j D^{-1} src by d
+// Jacobi sweeps y_1 = D^{-1}src + D^{-1}(src - (A D^{-1}) src),
+// y_j = y_{j-1} + D^{-1}(src - A y_{j-1}); one or two vectors at once.
+// Returns false if the grid must stop.
+template <typename T>
+__device__ bool neumann_apply(const SolverParams<T>& p, const T* src0, T* dst0, const T* src1, T* dst1,
+                              unsigned& epoch, int row0, int row1) {
+  const int d = p.degree;
+  const T* prev0 = nullptr;
+  const T* prev1 = nullptr;
+  for (int j = 1; j <= d; ++j) {
+    T* out0 = ((d - j) % 2 == 0) ? dst0 : p.tmpa;
+    T* out1 = ((d - j) % 2 == 0) ? dst1 : p.tmpb;
+    for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+      const T di = __ldg(p.dinv + i);
+      {
+        const T sv = src0[i];
+        if (j == 1) out0[i] = fma(di, sv - row_dot<T>(p.At, src0, i), di * sv);
+        else out0[i] = fma(di, sv - row_dot<T>(p.Au, prev0, i), prev0[i]);
+      }
+      if (src1) {
+        const T sv = src1[i];
+        if (j == 1) out1[i] = fma(di, sv - row_dot<T>(p.At, src1, i), di * sv);
+        else out1[i] = fma(di, sv - row_dot<T>(p.Au, prev1, i), prev1[i]);
+      }
+    }
+    if (!grid_barrier(p.bar, ++epoch, p.err, p.timeout_ns)) return false;
+    prev0 = out0;
+    prev1 = out1;
+  }
+  return true;
+}
+
+#define PBCG_HS 8
+
+// Eq. (rr), first half: r = b - A x in FP64 (FP64 values), s = A g with FP64 values,
+// and with Jacobi / no preconditioner also k = D^{-1} r, l = D^{-1} s and
+// nb = D^{-1} z_i (n_i stays the one computed from the old z_i, reading R6).
+// Publishes the partial ||b - A x||^2 to P2.  With write == false only the norm
+// is computed (stopping-test verification).
+template <typename T>
+__device__ bool replace_r1(const SolverParams<T>& p, void*, double* P2, double* smem, bool write,
+                           int row0, int row1) {
+  DAcc a_tr;
+  const bool neu = p.prec == 2;
+  for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+    const double r64 = p.b[i] - row_dot<double>(p.A64, p.x, i);
+    if (write) {
+      const T ri = T(r64);
+      const T si = T(row_dot<double>(p.A64, p.g, i));
+      p.r[i] = ri;
+      p.s[i] = si;
+      if (!neu) {
+        p.k[i] = minv_local(p, ri, i);
+        p.l[i] = minv_local(p, si, i);
+        p.nb[i] = minv_local(p, p.z[i], i);
+      }
+    }
+    a_tr.add(r64, r64);
+  }
+  double v1[1] = {a_tr.value()};
+  block_publish<1>(v1, smem, P2);
+  return true;
+}
+
+// Eq. (rr), second half (after a grid barrier): Neumann k = M^{-1} r, l = M^{-1} s;
+// then w = A k, z = A l and the line-21 partials of the replaced vectors into P1.
+template <typename T>
+__device__ bool replace_r2(const SolverParams<T>& p, double* P1, double* smem, unsigned& epoch,
+                           int row0, int row1) {
+  using Acc = typename AccOf<T>::type;
+  const bool neu = p.prec == 2;
+  if (neu && !neumann_apply(p, p.r, p.k, p.s, p.l, epoch, row0, row1)) return false;
+  Acc a_rr, a_rw, a_rs, a_rz, a_r2;
+  for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+    const T wi = neu ? row_dot<T>(p.Au, p.k, i) : row_dot<T>(p.At, p.r, i);
+    const T zi = neu ? row_dot<T>(p.Au, p.l, i) : row_dot<T>(p.At, p.s, i);
+    p.w[i] = wi;
+    p.z[i] = zi;
+    const T rh = p.rh[i], ri = p.r[i], si = p.s[i];
+    a_rr.add(rh, ri); a_rw.add(rh, wi); a_rs.add(rh, si); a_rz.add(rh, zi); a_r2.add(ri, ri);
+  }
+  double v5[5] = {a_rr.value(), a_rw.value(), a_rs.value(), a_rz.value(), a_r2.value()};
+  block_publish<5>(v5, smem, P1);
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverParams<T> p) {
+  using Acc = typename AccOf<T>::type;
+  __shared__ double smem[32 * kMaxDots];
+  const int n = p.n;
+  const int row0 = (int)min((long long)n, (long long)blockIdx.x * p.chunk);
+  const int row1 = min(n, row0 + p.chunk);
+  const bool neu = p.prec == 2;
+  unsigned epoch = 0;
+  double* P0 = p.part;
+  double* P1 = p.part + gridDim.x * kMaxDots;
+  double* P2 = p.part + 2 * gridDim.x * kMaxDots;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  int nrep = 0;
+
+#define PBCG_SYNC() \
+  do { if (!grid_barrier(p.bar, ++epoch, p.err, p.timeout_ns)) return; } while (0)
+#define PBCG_ROWS for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x)
+#define PBCG_FINISH(st, its, rnv)                                                        \
+  do {                                                                                   \
+    if (leader) {                                                                        \
+      p.res->status = (st); p.res->iterations = (its); p.res->nrep = nrep;               \
+      p.res->rn_rel = (rnv) / bn;                                                        \
+    }                                                                                    \
+    return;                                                                              \
+  } while (0)
+
+  // ---------------- initialisation (Algorithm 2, lines 2-3)
+  {
+    Acc a_rr;
+    DAcc a_bb;
+    PBCG_ROWS {
+      const double bi = p.b[i];
+      const double r64 = bi - row_dot<double>(p.A64, p.x, i);
+      const T ri = T(r64);
+      p.r[i] = ri;
+      p.rh[i] = ri;
+      if (!neu) p.k[i] = minv_local(p, ri, i);
+      p.g[i] = T(0); p.s[i] = T(0); p.l[i] = T(0); p.z[i] = T(0); p.v[i] = T(0);
+      if (neu) p.nn[i] = T(0);
+      a_rr.add(ri, ri);
+      a_bb.add(bi, bi);
+    }
+    double v2[2] = {a_rr.value(), a_bb.value()};
+    block_publish<2>(v2, smem, P0);
+  }
+  PBCG_SYNC();
+  if (neu && !neumann_apply(p, p.r, p.k, (const T*)nullptr, (T*)nullptr, epoch, row0, row1)) return;
+  {
+    Acc a_rw;
+    PBCG_ROWS {
+      const T wi = neu ? row_dot<T>(p.Au, p.k, i) : row_dot<T>(p.At, p.r, i);  // w_0 = A k_0
+      p.w[i] = wi;
+      a_rw.add(p.rh[i], wi);
+    }
+    double v1[1] = {a_rw.value()};
+    block_publish<1>(v1, smem, P1);
+  }
+  PBCG_SYNC();
+  double rho, rw0, bn, rn;
+  {
+    double t2[2];
+    grid_combine<2>(P0, t2, smem);
+    double t1[1];
+    grid_combine<1>(P1, t1, smem);
+    rho = t2[0];
+    bn = sqrt(t2[1]);
+    rw0 = t1[0];
+    rn = sqrt(rho);
+  }
+  if (leader) { p.res->bnorm = bn; p.res->rn0 = rn; p.res->true_rel = -1.0; }
+  if (bn == 0.0) {            // b = 0: x = 0
+    PBCG_ROWS { p.x[i] = 0.0; }
+    if (leader) { p.res->status = kOK; p.res->iterations = 0; p.res->nrep = 0; p.res->rn_rel = 0.0; }
+    return;
+  }
+  if (rn <= p.tol * bn) PBCG_FINISH(kOK, 0, rn);
+  double alpha = rw0 != 0.0 ? rho / rw0 : INFINITY;
+  if (rw0 == 0.0 || !isfinite(alpha)) PBCG_FINISH(kBreakdown, 0, rn);
+  double beta = 0.0, omega_prev = 0.0;
+  const double rn0 = rn;
+  double rn_last_rr = rn;
+  bool rep_last = false;
+  const double sqrt_eps = 1.4901161193847656e-08;  // sqrt(2^-52)
+
+  for (int it = 0; it < p.max_it; ++it) {
+    // ---------------- m_i = M^{-1} w_i (Neumann only; on the fly otherwise)
+    if (neu && !neumann_apply(p, p.w, p.m, (const T*)nullptr, (T*)nullptr, epoch, row0, row1)) return;
+    // ---------------- pass A: t_i = A m_i; lines 5-11; partials of line 12
+    {
+      const T aT = T(alpha), bT = T(beta), opT = T(omega_prev);
+      Acc a_qy, a_yy;
+      PBCG_ROWS {
+        const T wi = p.w[i];
+        const T mi = neu ? p.m[i] : minv_local(p, wi, i);
+        const T ti = neu ? row_dot<T>(p.Au, p.m, i) : row_dot<T>(p.At, p.w, i);
+        const T zo = p.z[i];
+        const T np = neu ? p.nn[i] : (rep_last ? p.nb[i] : minv_local(p, zo, i));   // n_{i-1}
+        const T kk = p.k[i], gg = p.g[i], ll = p.l[i], ss = p.s[i], vv = p.v[i], rr = p.r[i];
+        const T gn = fma(bT, fma(-opT, ll, gg), kk);   // g_i = k_i + beta_i (g_{i-1} - omega_{i-1} l_{i-1})
+        const T sn = fma(bT, fma(-opT, zo, ss), wi);   // s_i = w_i + beta_i (s_{i-1} - omega_{i-1} z_{i-1})
+        const T ln = fma(bT, fma(-opT, np, ll), mi);   // l_i = m_i + beta_i (l_{i-1} - omega_{i-1} n_{i-1})
+        const T zn = fma(bT, fma(-opT, vv, zo), ti);   // z_i = t_i + beta_i (z_{i-1} - omega_{i-1} v_{i-1})
+        const T q = fma(-aT, sn, rr);                  // q_i = r_i - alpha_i s_i
+        const T y = fma(-aT, zn, wi);                  // y_i = w_i - alpha_i z_i
+        p.g[i] = gn; p.s[i] = sn; p.l[i] = ln; p.z[i] = zn; p.t[i] = ti;
+        a_qy.add(q, y);
+        a_yy.add(y, y);
+      }
+      double v2[2] = {a_qy.value(), a_yy.value()};
+      block_publish<2>(v2, smem, P0);
+    }
+    PBCG_SYNC();
+    // ---------------- n_i = M^{-1} z_i (Neumann only), overlapping the reduction
+    if (neu && !neumann_apply(p, p.z, p.nn, (const T*)nullptr, (T*)nullptr, epoch, row0, row1)) return;
+    double omega;
+    {
+      double t2[2];
+      grid_combine<2>(P0, t2, smem);
+      omega = t2[1] == 0.0 ? 0.0 : t2[0] / t2[1];     // line 16
+    }
+    if (!isfinite(omega)) PBCG_FINISH(kBreakdown, it, rn);
+    bool do_rr = false;
+    if (p.rr_period > 0 && it > 0 && it % p.rr_period == 0 && rn >= sqrt_eps * rn0) do_rr = true;
+    if (p.rr_theta > 0.0 && rn <= p.rr_theta * rn_last_rr) do_rr = true;
+    // ---------------- pass B: v_i = A n_i; lines 17-20; partials of line 21
+    {
+      const T aT = T(alpha), oT = T(omega);
+      Acc a_rr, a_rw, a_rs, a_rz, a_r2;
+      const bool hist = it < p.K;
+      PBCG_ROWS {
+        const T zi = p.z[i];
+        const T ni = neu ? p.nn[i] : minv_local(p, zi, i);
+        const T vi = neu ? row_dot<T>(p.Au, p.nn, i) : row_dot<T>(p.At, p.z, i);
+        const T wi = p.w[i];
+        const T mi = neu ? p.m[i] : minv_local(p, wi, i);
+        const T rr = p.r[i], ss = p.s[i], kk = p.k[i], ll = p.l[i], gg = p.g[i], ti = p.t[i];
+        const T q = fma(-aT, ss, rr);
+        const T u = fma(-aT, ll, kk);
+        const T y = fma(-aT, zi, wi);
+        const double xn = fma(omega, (double)u, fma(alpha, (double)gg, p.x[i]));  // line 17
+        const T rn1 = fma(-oT, y, q);                    // r_{i+1} = q_i - omega_i y_i
+        const T kn = fma(-oT, fma(-aT, ni, mi), u);      // k_{i+1} = u_i - omega_i (m_i - alpha_i n_i)
+        const T wn = fma(-oT, fma(-aT, vi, ti), y);      // w_{i+1} = y_i - omega_i (t_i - alpha_i v_i)
+        p.x[i] = xn; p.v[i] = vi; p.r[i] = rn1; p.k[i] = kn; p.w[i] = wn;
+        if (hist) p.hist_x[(size_t)it * n + i] = xn;
+        if (!do_rr) {
+          const T rh = p.rh[i];
+          a_rr.add(rh, rn1); a_rw.add(rh, wn); a_rs.add(rh, ss); a_rz.add(rh, zi); a_r2.add(rn1, rn1);
+        }
+      }
+      if (!do_rr) {
+        double v5[5] = {a_rr.value(), a_rw.value(), a_rs.value(), a_rz.value(), a_r2.value()};
+        block_publish<5>(v5, smem, P1);
+      }
+    }
+    // ---------------- residual replacement, Eq. (rr), after line 20 (reading R6)
+    if (do_rr) {
+      PBCG_SYNC();
+      if (!replace_r1(p, nullptr, P2, smem, true, row0, row1)) return;
+      PBCG_SYNC();
+      if (!replace_r2(p, P1, smem, epoch, row0, row1)) return;
+      ++nrep;
+    }
+    rep_last = do_rr;
+    PBCG_SYNC();
+    // ---------------- lines 21-26: second reduction, stopping test, beta, alpha
+    double t5[5];
+    grid_combine<5>(P1, t5, smem);
+    double rho_new = t5[0], rw = t5[1], rs = t5[2], rz = t5[3];
+    rn = sqrt(t5[4]);
+    if (rn <= p.tol * bn) {
+      // reading R5: verify with the FP64 true residual; with a replacement policy a
+      // failed check forces a replacement, without one the solve has stagnated.
+      const bool any_rr = p.rr_period > 0 || p.rr_theta > 0.0;
+      if (!replace_r1(p, nullptr, P2, smem, any_rr, row0, row1)) return;
+      PBCG_SYNC();
+      double t1[1];
+      grid_combine<1>(P2, t1, smem);
+      const double true_rn = sqrt(t1[0]);
+      if (leader) p.res->true_rel = true_rn / bn;
+      if (true_rn <= p.tol * bn || !any_rr) {
+        if (leader && it < p.hist_len) {
+          double* h = p.hist_s + (size_t)it * PBCG_HS;
+          h[0] = alpha; h[1] = omega; h[2] = NAN; h[3] = rn / bn; h[4] = do_rr ? 1.0 : 0.0;
+        }
+        PBCG_FINISH(true_rn <= p.tol * bn ? kOK : kStagnated, it + 1, rn);
+      }
+      if (!replace_r2(p, P1, smem, epoch, row0, row1)) return;
+      ++nrep;
+      rep_last = true;
+      do_rr = true;
+      PBCG_SYNC();
+      grid_combine<5>(P1, t5, smem);
+      rho_new = t5[0]; rw = t5[1]; rs = t5[2]; rz = t5[3];
+      rn = sqrt(t5[4]);
+    }
+    if (do_rr) rn_last_rr = rn;
+    if (omega == 0.0 || rho == 0.0) PBCG_FINISH(kBreakdown, it + 1, rn);
+    const double beta_new = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_new, rho));          // line 25
+    const double den = __dsub_rn(__dadd_rn(rw, __dmul_rn(beta_new, rs)), __dmul_rn(__dmul_rn(beta_new, omega), rz));
+    const double alpha_new = den != 0.0 ? __ddiv_rn(rho_new, den) : INFINITY;                       // line 26
+    if (leader && it < p.hist_len) {
+      double* h = p.hist_s + (size_t)it * PBCG_HS;
+      h[0] = alpha; h[1] = omega; h[2] = beta_new; h[3] = rn / bn; h[4] = do_rr ? 1.0 : 0.0;
+    }
+    if (!(isfinite(beta_new) && den != 0.0 && isfinite(alpha_new))) PBCG_FINISH(kBreakdown, it + 1, rn);
+    alpha = alpha_new;
+    beta = beta_new;
+    omega_prev = omega;
+    rho = rho_new;
+  }
+  PBCG_FINISH(kNotConverged, p.max_it, rn);
+#undef PBCG_SYNC
+#undef PBCG_ROWS
+#undef PBCG_FINISH
+}
+
+}  // namespace pbcg
