@@ -149,7 +149,8 @@ def run_gpu(args):
 
     results = {}
     clocks = None
-    for name in (args.precision,) + tuple(k for k in variants if k != args.precision):
+    order = (args.precision,) + (() if args.only else tuple(k for k in variants if k != args.precision))
+    for name in order:
         for _ in range(args.warmup):
             one(name)
         if world > 1:
@@ -185,14 +186,14 @@ def run_gpu(args):
     b_pin = torch.from_numpy(prob.b).pin_memory()
     x_pin = torch.zeros(n, dtype=torch.float64).pin_memory()
     e2e_times = []
-    for k in range(max(1, args.steps)):
+    for k in range(0 if args.no_e2e else max(1, args.steps)):
         x_pin.zero_()
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, res = solvers[args.precision].solve_host(b_pin.numpy(), x_pin.numpy())
         e2e_times.append((time.perf_counter() - t0) * 1e3)
-    e2e = {"value": statistics.mean(e2e_times), "unit": "ms", "h2d_bytes_per_step": 2 * 8 * n,
+    e2e = {"value": statistics.mean(e2e_times) if e2e_times else None, "unit": "ms", "h2d_bytes_per_step": 2 * 8 * n,
            "d2h_bytes_per_step": 8 * n + 64}
 
     # roofline of the dominant kernel (the persistent solver)
@@ -323,6 +324,8 @@ def main():
     ap.add_argument("--max-it", type=int, default=20000)
     ap.add_argument("--cpu-iters", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", action="store_true", help="measure the headline variant only")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -161,6 +161,69 @@ pbcg_status pbicgstab_destroy(pbcg_ctx* ctx);
 /* Thread-local description of the last failure in this thread ("" if none). */
 const char* pbicgstab_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Batched solves: many independent systems A_k x_k = b_k of different sizes,
+ * solved by one persistent kernel launch (replayed from a CUDA graph).  Each
+ * system is solved by one thread block running Algorithm 2 with Eq. (rr)
+ * replacements; blocks take systems from a device queue, largest first.
+ *
+ * Storage: the systems' CSR matrices are concatenated.  For system k (0-based):
+ *   rows       row_off[k] .. row_off[k+1]-1 of the concatenated b and x,
+ *   row_ptr    row_ptr[row_off[k] + k .. row_off[k+1] + k] (n_k + 1 entries,
+ *              local: starting at 0),
+ *   col / val  col[nnz_off[k] + e], val[nnz_off[k] + e] with LOCAL column
+ *              indices 0 .. n_k-1.
+ * row_off and nnz_off (n_sys + 1 int64 each) are HOST arrays; row_ptr, col, val
+ * are device arrays.  Preconditioner: NONE or JACOBI (per system). */
+typedef struct pbcg_batch {
+  int32_t n_sys;
+  int32_t val_dtype;        /* pbcg_dtype */
+  const int64_t* row_off;   /* host, n_sys + 1 */
+  const int64_t* nnz_off;   /* host, n_sys + 1 */
+  const int32_t* row_ptr;   /* device */
+  const int32_t* col;       /* device */
+  const void* val;          /* device */
+  int32_t precond;          /* PBCG_PREC_NONE or PBCG_PREC_JACOBI */
+  int32_t reserved0;
+} pbcg_batch;
+
+/* Per-system outputs, HOST arrays of n_sys entries (any may be NULL). */
+typedef struct pbcg_batch_result {
+  int32_t* status;
+  int32_t* iterations;
+  int32_t* n_replacements;
+  double* rel_res_true;     /* ||b_k - A_k x_k|| / ||b_k||, FP64 */
+  double time_ms;           /* device time of the batched solve kernel */
+  int32_t n_ok;             /* systems with status PBCG_OK */
+  int32_t block_threads;    /* launch shape used (autotuned when the options ask for 0) */
+  int32_t grid_blocks;
+  int32_t reserved0;
+} pbcg_batch_result;
+
+typedef struct pbcg_batch_ctx pbcg_batch_ctx;
+
+/* Validate and prepare a batch (copies of the matrices, D^{-1}, A D^{-1}, FP32
+ * copies in mixed mode, workspace, queue order).  opt: precision, tol, max_it,
+ * replacement policy; grid_blocks / block_threads = 0 request the autotuner
+ * (it times the candidate launch shapes on the first solve and keeps the
+ * fastest).  History options are ignored.  Errors: INVALID_ARG, OUT_OF_MEMORY,
+ * CUDA_ERROR. */
+pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_batch* batch,
+                                   const pbcg_options* opt, void* stream);
+
+/* Solve all systems: b (device, sum n_k doubles), x (device, read as x0 and
+ * overwritten).  res: host or NULL (NULL: enqueue only).  The launch is a CUDA
+ * graph replay after the first call with the same b and x pointers.  Returns
+ * PBCG_OK when every system converged, else the first failing status found. */
+pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* ctx, const double* b, double* x,
+                                  pbcg_batch_result* res);
+
+pbcg_status pbicgstab_batch_destroy(pbcg_batch_ctx* ctx);
+
+/* One-shot convenience: create, solve, destroy. */
+pbcg_status pbicgstab_solve_batched(const pbcg_batch* batch, const pbcg_options* opt, void* stream,
+                                    const double* b, double* x, pbcg_batch_result* res);
+
 /* Test hook for the fault-detection path: launches a cooperative grid whose
  * blocks wait at a barrier for `extra_arrivals` more blocks than exist, so the
  * wait can only end by its timeout.  Returns PBCG_OK when the kernel gave up

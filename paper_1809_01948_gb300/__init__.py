@@ -14,7 +14,7 @@ import torch
 from . import _capi as capi
 from ._capi import Result, STATUS_NAMES  # noqa: F401
 
-__all__ = ["Solver", "PBCGError", "build", "STATUS_NAMES", "test_barrier_timeout"]
+__all__ = ["Solver", "BatchSolver", "PBCGError", "build", "STATUS_NAMES", "test_barrier_timeout"]
 
 
 class PBCGError(RuntimeError):
@@ -168,6 +168,73 @@ class Solver:
     def close(self):
         if getattr(self, "ctx", None):
             _lib().pbicgstab_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """Many independent CSR systems solved by one persistent launch (``pbicgstab_batch_*``).
+
+    ``row_off``/``nnz_off``: host int64 arrays (n_sys + 1); ``row_ptr`` (local per
+    system, concatenated: n_k + 1 entries each), ``col`` (local indices), ``val``:
+    CUDA tensors.  grid_blocks = block_threads = 0 lets the library autotune.
+    """
+
+    def __init__(self, row_off, nnz_off, row_ptr, col, val, precond: str = "jacobi", precision: str = "mixed",
+                 tol: float = 1e-8, max_it: int = 1000, rr_period: int = 0, rr_theta: float = 0.0,
+                 grid_blocks: int = 0, block_threads: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        import numpy as np
+        lib = _lib()
+        self.row_off = np.ascontiguousarray(row_off, dtype=np.int64)
+        self.nnz_off = np.ascontiguousarray(nnz_off, dtype=np.int64)
+        self.n_sys = len(self.row_off) - 1
+        self.total_rows = int(self.row_off[-1])
+        row_ptr = row_ptr.to(torch.int32).contiguous()
+        col = col.to(torch.int32).contiguous()
+        val = val.contiguous()
+        bt = capi.Batch()
+        bt.n_sys = self.n_sys
+        bt.val_dtype = capi.F64 if val.dtype == torch.float64 else capi.F32
+        bt.row_off = self.row_off.ctypes.data_as(C.c_void_p)
+        bt.nnz_off = self.nnz_off.ctypes.data_as(C.c_void_p)
+        bt.row_ptr, bt.col, bt.val = _ptr(row_ptr), _ptr(col), _ptr(val)
+        bt.precond = _PREC[precond]
+        self.opt = capi.Options()
+        _check(lib.pbicgstab_default_options(C.byref(self.opt)), "default_options")
+        self.opt.precision = _PRECISION[precision]
+        self.opt.tol, self.opt.max_it = tol, max_it
+        self.opt.rr_period, self.opt.rr_theta = rr_period, rr_theta
+        self.opt.grid_blocks, self.opt.block_threads = grid_blocks, block_threads
+        self.ctx = C.c_void_p()
+        _check(lib.pbicgstab_batch_create(C.byref(self.ctx), C.byref(bt), C.byref(self.opt), _stream_handle(stream)),
+               "pbicgstab_batch_create")
+
+    def solve(self, b: torch.Tensor, x: Optional[torch.Tensor] = None):
+        """Returns (x, info dict with per-system numpy arrays)."""
+        import numpy as np
+        if x is None:
+            x = torch.zeros_like(b)
+        st = np.zeros(self.n_sys, np.int32)
+        it = np.zeros(self.n_sys, np.int32)
+        nr = np.zeros(self.n_sys, np.int32)
+        tr = np.zeros(self.n_sys, np.float64)
+        res = capi.BatchResult()
+        res.status, res.iterations = st.ctypes.data_as(C.c_void_p), it.ctypes.data_as(C.c_void_p)
+        res.n_replacements, res.rel_res_true = nr.ctypes.data_as(C.c_void_p), tr.ctypes.data_as(C.c_void_p)
+        code = _lib().pbicgstab_batch_solve(self.ctx, _ptr(b), _ptr(x), C.byref(res))
+        if code in (capi.PBCG_INVALID_ARG, capi.PBCG_CUDA_ERROR, capi.PBCG_OUT_OF_MEMORY, capi.PBCG_TIMEOUT):
+            raise PBCGError(code, capi.last_error())
+        return x, dict(status=st, iterations=it, n_replacements=nr, rel_res_true=tr, time_ms=res.time_ms,
+                       n_ok=res.n_ok, block_threads=res.block_threads, grid_blocks=res.grid_blocks)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _lib().pbicgstab_batch_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

@@ -47,6 +47,18 @@ class Result(C.Structure):
                     rel_res_true=self.rel_res_true, time_ms=self.time_ms)
 
 
+class Batch(C.Structure):
+    _fields_ = [("n_sys", C.c_int32), ("val_dtype", C.c_int32), ("row_off", C.c_void_p), ("nnz_off", C.c_void_p),
+                ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p), ("precond", C.c_int32),
+                ("reserved0", C.c_int32)]
+
+
+class BatchResult(C.Structure):
+    _fields_ = [("status", C.c_void_p), ("iterations", C.c_void_p), ("n_replacements", C.c_void_p),
+                ("rel_res_true", C.c_void_p), ("time_ms", C.c_double), ("n_ok", C.c_int32),
+                ("block_threads", C.c_int32), ("grid_blocks", C.c_int32), ("reserved0", C.c_int32)]
+
+
 # name -> (restype, argtypes)
 PROTOTYPES = {
     "pbicgstab_default_options": (C.c_int, [C.POINTER(Options)]),
@@ -60,6 +72,11 @@ PROTOTYPES = {
     "pbicgstab_destroy": (C.c_int, [C.c_void_p]),
     "pbicgstab_last_error": (C.c_char_p, []),
     "pbicgstab_test_barrier_timeout": (C.c_int, [C.c_double, C.c_int32, C.POINTER(C.c_int32)]),
+    "pbicgstab_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Batch), C.POINTER(Options), C.c_void_p]),
+    "pbicgstab_batch_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BatchResult)]),
+    "pbicgstab_batch_destroy": (C.c_int, [C.c_void_p]),
+    "pbicgstab_solve_batched": (C.c_int, [C.POINTER(Batch), C.POINTER(Options), C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.POINTER(BatchResult)]),
 }
 
 _lib = None

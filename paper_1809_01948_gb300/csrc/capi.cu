@@ -144,7 +144,7 @@ __global__ void fold_dia_kernel(int n, MatView<double> src, const double* dinv, 
 
 // FP64 ||b - A x||^2 and ||b||^2, block partials then one fixed-order final sum.
 __global__ void true_res_partial_kernel(MatView<double> A, const double* b, const double* x, double* part) {
-  __shared__ double smem[32 * kMaxDots];
+  __shared__ double smem[32 * 8 + kMaxDots];
   double v[2] = {0.0, 0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
     const double r = b[i] - row_dot<double>(A, x, i);
@@ -155,7 +155,7 @@ __global__ void true_res_partial_kernel(MatView<double> A, const double* b, cons
 }
 
 __global__ void true_res_final_kernel(const double* part, int nparts, double* out) {
-  __shared__ double smem[32 * kMaxDots];
+  __shared__ double smem[32 * 8 + kMaxDots];
   double v[2] = {0.0, 0.0};
   for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
     v[0] += part[b * kMaxDots + 0];
@@ -310,8 +310,8 @@ static pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads) {
   if (max_coresident <= 0) return set_error(PBCG_INVALID_ARG, "kernel cannot be resident with %d threads per block", nt);
   int g = c->opt.grid_blocks;
   if (g == 0) {
-    // about 4 rows per thread at most 2 blocks per SM; tiny systems use fewer blocks
-    const long long want = (c->n + (long long)nt * 4 - 1) / ((long long)nt * 4);
+    // every SM busy (up to 2 blocks per SM), but at least 32 rows per block
+    const long long want = (c->n + 31) / 32;
     g = (int)std::min<long long>(std::max<long long>(1, want), (long long)std::min(max_coresident, 2 * sms));
   }
   if (g > max_coresident)
@@ -351,6 +351,7 @@ static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
     if (c->nnz)
       CK(cudaMemcpyAsync(c->col, A->col, sizeof(int) * c->nnz, cudaMemcpyDeviceToDevice, c->stream), "copy col");
     validate_csr_kernel<<<nb, 256, 0, c->stream>>>(n, c->nnz, c->row_ptr, c->col, A->val, f32, need_diag, dflags, c->diag64);
+    CK(cudaGetLastError(), "validate kernel launch");
   } else {
     nval = (long long)c->ndiag * n;
     MatView<double> offs;
@@ -563,7 +564,7 @@ static pbcg_status collect(pbcg_ctx* c, pbcg_result* res) {
   CK(cudaStreamSynchronize(c->stream), "solve");
   const DevState& h = *c->hstate;
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "event timing");
   memset(res, 0, sizeof *res);
   res->status = h.err ? PBCG_TIMEOUT : h.res.status;
   res->iterations = h.res.iterations;

@@ -102,52 +102,112 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned epoch, 
 }
 
 // ---------------------------------------------------------------- reductions
-// Block-wide sum of ND doubles per thread, deterministic (fixed shuffle tree, fixed
-// warp order).  The result is returned to every thread.  smem: >= 32*ND doubles.
-template <int ND>
-__device__ __forceinline__ void block_sum(double (&v)[ND], double* smem) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// FP64 arithmetic is scarce on GB300 (about 2 lane-FMAs per SM per cycle), so the
+// reductions are written to issue few FP64 instructions:
+//  * warp level: a "transpose" butterfly.  With P (power of two) values per lane,
+//    the first log2(P) shuffle levels exchange half of the values and halve the
+//    count, so P values cost P-1 adds plus the remaining plain levels (8 values: 9
+//    adds instead of 40).  Afterwards lane l holds the total of value
+//    vidx<P>(l).
+//  * block level: one value per (warp, index) in shared memory, reduced by warp 0.
+//  * grid level: warp 0 of every block sums all blocks' partials in a fixed order.
+// All orders are fixed, so results are bitwise reproducible for a given launch
+// shape, and every block obtains bit-identical totals.
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int P>
+__device__ __forceinline__ int vidx(int lane) {
+  int j = 0;
 #pragma unroll
-  for (int d = 0; d < ND; ++d) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[d] += __shfl_xor_sync(0xffffffffu, v[d], o);
-  }
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int d = 0; d < ND; ++d) smem[d * 32 + wid] = v[d];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    double s = (lane < nw) ? smem[d * 32 + lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    v[d] = s;
-  }
+  for (int k = 0, off = 16; (1 << k) < P; ++k, off >>= 1) j |= ((lane & off) ? 1 : 0) << k;
+  return j;
 }
 
-// Write this block's ND partial sums to part[blockIdx.x * kMaxDots + d].
+template <int P>
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[P]) {
+  const int lane = threadIdx.x & 31;
+  int off = 16;
+#pragma unroll
+  for (int cnt = P; cnt > 1; cnt >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int j = 0; j < cnt / 2; ++j) {
+      const double keep = upper ? v[2 * j + 1] : v[2 * j];
+      const double send = upper ? v[2 * j] : v[2 * j + 1];
+      v[j] = keep + __shfl_xor_sync(kFull, send, off);
+    }
+    off >>= 1;
+  }
+  double s = v[0];
+#pragma unroll
+  for (; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+  return s;
+}
+
+template <int ND> struct Pad { static constexpr int value = ND <= 1 ? 1 : ND <= 2 ? 2 : ND <= 4 ? 4 : 8; };
+
+// Block-wide sums of ND per-thread doubles; block totals land in out_smem[0..ND)
+// (valid after the trailing __syncthreads).  work_smem: >= 32 * 8 doubles.
+template <int ND>
+__device__ __forceinline__ void block_reduce(const double (&in)[ND], double* work_smem, double* out_smem) {
+  constexpr int P = Pad<ND>::value;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double v[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) v[j] = j < ND ? in[j] : 0.0;
+  const double s = warp_transpose_sum<P>(v);
+  const int j = vidx<P>(lane);
+  if ((lane & (32 / P - 1)) == 0) work_smem[j * 32 + wid] = s;
+  __syncthreads();
+  if (wid == 0) {
+    double w[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) w[q] = lane < nw ? work_smem[q * 32 + lane] : 0.0;
+    const double t = warp_transpose_sum<P>(w);
+    if ((lane & (32 / P - 1)) == 0 && j < ND) out_smem[j] = t;
+  }
+  __syncthreads();
+}
+
+// Block totals of ND per-thread values written to part[blockIdx.x * kMaxDots + d].
 template <int ND>
 __device__ __forceinline__ void block_publish(double (&v)[ND], double* smem, double* part) {
-  block_sum<ND>(v, smem);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int d = 0; d < ND; ++d) part[blockIdx.x * kMaxDots + d] = v[d];
-  }
+  block_reduce<ND>(v, smem, smem + 32 * 8);
+  if (threadIdx.x < ND) part[blockIdx.x * kMaxDots + threadIdx.x] = smem[32 * 8 + threadIdx.x];
 }
 
-// After a grid barrier: every block sums all blocks' partials in the same fixed
+// Block-wide sum returning the totals to every thread (used outside the solver loop).
+template <int ND>
+__device__ __forceinline__ void block_sum(double (&v)[ND], double* smem) {
+  block_reduce<ND>(v, smem, smem + 32 * 8);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) v[d] = smem[32 * 8 + d];
+  __syncthreads();
+}
+
+// After a grid barrier: warp 0 of every block sums all blocks' partials in one fixed
 // order, so every block obtains bit-identical totals (the GLRED result).
 template <int ND>
 __device__ __forceinline__ void grid_combine(const double* part, double (&out)[ND], double* smem) {
+  constexpr int P = Pad<ND>::value;
+  const int lane = threadIdx.x & 31;
+  double* res = smem + 32 * 8;
+  if (threadIdx.x < 32) {
+    double v[P];
 #pragma unroll
-  for (int d = 0; d < ND; ++d) out[d] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int j = 0; j < P; ++j) v[j] = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
 #pragma unroll
-    for (int d = 0; d < ND; ++d) out[d] += __ldcg(part + b * kMaxDots + d);
+      for (int d = 0; d < ND; ++d) v[d] += __ldcg(part + b * kMaxDots + d);
+    }
+    const double t = warp_transpose_sum<P>(v);
+    const int j = vidx<P>(lane);
+    if ((lane & (32 / P - 1)) == 0 && j < ND) res[j] = t;
   }
-  block_sum<ND>(out, smem);
+  __syncthreads();
+#pragma unroll
+  for (int d = 0; d < ND; ++d) out[d] = res[d];
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------- dot accumulators

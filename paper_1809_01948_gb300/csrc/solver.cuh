@@ -37,19 +37,20 @@ struct DevResult {
   double true_rel; // set when the in-kernel true residual was evaluated (else -1)
 };
 
-template <typename T>
+template <typename T, typename VR = double>
 struct SolverParams {
   int n, chunk;
   MatView<T> At;        // hot operator: A D^{-1} (Jacobi, and Neumann's first sweep) or A (none)
   MatView<T> Au;        // A in the vector precision (Neumann sweeps, t = A m, v = A n)
-  MatView<double> A64;  // A in FP64: initial and replacement residuals
+  MatView<VR> A64;      // A with its stored values (FP64, or FP32 widened exactly): initial
+                        // and replacement residuals, evaluated in FP64
   const T* dinv;        // D^{-1} (nullptr without preconditioner)
   int prec;             // 0 none, 1 Jacobi, 2 Neumann
   int degree;
   const double* b;
   double* x;
   T *r, *rh, *k, *w, *g, *s, *l, *z, *v, *t, *nb, *m, *nn, *tmpa, *tmpb;
-  double* part;         // 3 partial sets of gridDim.x * kMaxDots doubles
+  double* part;         // grid team: 3 partial sets of gridDim.x * kMaxDots doubles
   unsigned* bar;
   int* err;
   DevResult* res;
@@ -64,8 +65,51 @@ struct SolverParams {
   unsigned long long timeout_ns;
 };
 
-template <typename T>
-__device__ __forceinline__ T minv_local(const SolverParams<T>& p, T v, int i) {
+// ---------------------------------------------------------------------------
+// Synchronisation scopes.  The algorithm body is written once against a "team":
+//  GridTeam  -- the whole cooperative grid solves one system; sync() is the
+//               grid barrier with timeout, dot partials go through global memory.
+//  BlockTeam -- one thread block solves one system (batched solver); sync() is
+//               __syncthreads and the partials stay in shared memory.
+// Both give every thread of the team bit-identical reduction results.
+struct GridTeam {
+  int row0, row1;
+  unsigned epoch;
+  unsigned* bar;
+  int* err;
+  unsigned long long timeout_ns;
+  double* part;
+  double* smem;   // >= 32*8 + kMaxDots doubles
+  __device__ __forceinline__ bool sync() { return grid_barrier(bar, ++epoch, err, timeout_ns); }
+  template <int ND>
+  __device__ __forceinline__ void publish(double (&v)[ND], int set) {
+    block_publish<ND>(v, smem, part + (size_t)set * gridDim.x * kMaxDots);
+  }
+  template <int ND>
+  __device__ __forceinline__ void combine(int set, double (&out)[ND]) {
+    grid_combine<ND>(part + (size_t)set * gridDim.x * kMaxDots, out, smem);
+  }
+  __device__ __forceinline__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+};
+
+struct BlockTeam {
+  int row0, row1;
+  double* smem;   // >= 32*8 + 3*kMaxDots doubles
+  __device__ __forceinline__ bool sync() { __syncthreads(); return true; }
+  template <int ND>
+  __device__ __forceinline__ void publish(double (&v)[ND], int set) {
+    block_reduce<ND>(v, smem, smem + 32 * 8 + set * kMaxDots);
+  }
+  template <int ND>
+  __device__ __forceinline__ void combine(int set, double (&out)[ND]) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) out[d] = smem[32 * 8 + set * kMaxDots + d];
+  }
+  __device__ __forceinline__ bool leader() const { return threadIdx.x == 0; }
+};
+
+template <typename T, typename VR>
+__device__ __forceinline__ T minv_local(const SolverParams<T, VR>& p, T v, int i) {
   return p.prec == 1 ? T(__ldg(p.dinv + i) * v) : v;
 }
 
@@ -73,9 +117,10 @@ __device__ __forceinline__ T minv_local(const SolverParams<T>& p, T v, int i) {
 // Jacobi sweeps y_1 = D^{-1}src + D^{-1}(src - (A D^{-1}) src),
 // y_j = y_{j-1} + D^{-1}(src - A y_{j-1}); one or two vectors at once.
 // Returns false if the grid must stop.
-template <typename T>
-__device__ bool neumann_apply(const SolverParams<T>& p, const T* src0, T* dst0, const T* src1, T* dst1,
-                              unsigned& epoch, int row0, int row1) {
+template <typename T, typename VR, typename Team>
+__device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T* src0, T* dst0, const T* src1,
+                              T* dst1) {
+  const int row0 = team.row0, row1 = team.row1;
   const int d = p.degree;
   const T* prev0 = nullptr;
   const T* prev1 = nullptr;
@@ -95,7 +140,7 @@ __device__ bool neumann_apply(const SolverParams<T>& p, const T* src0, T* dst0, 
         else out1[i] = fma(di, sv - row_dot<T>(p.Au, prev1, i), prev1[i]);
       }
     }
-    if (!grid_barrier(p.bar, ++epoch, p.err, p.timeout_ns)) return false;
+    if (!team.sync()) return false;
     prev0 = out0;
     prev1 = out1;
   }
@@ -109,9 +154,9 @@ __device__ bool neumann_apply(const SolverParams<T>& p, const T* src0, T* dst0, 
 // nb = D^{-1} z_i (n_i stays the one computed from the old z_i, reading R6).
 // Publishes the partial ||b - A x||^2 to P2.  With write == false only the norm
 // is computed (stopping-test verification).
-template <typename T>
-__device__ bool replace_r1(const SolverParams<T>& p, void*, double* P2, double* smem, bool write,
-                           int row0, int row1) {
+template <typename T, typename VR, typename Team>
+__device__ void replace_r1(const SolverParams<T, VR>& p, Team& team, bool write) {
+  const int row0 = team.row0, row1 = team.row1;
   DAcc a_tr;
   const bool neu = p.prec == 2;
   for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
@@ -130,18 +175,17 @@ __device__ bool replace_r1(const SolverParams<T>& p, void*, double* P2, double* 
     a_tr.add(r64, r64);
   }
   double v1[1] = {a_tr.value()};
-  block_publish<1>(v1, smem, P2);
-  return true;
+  team.template publish<1>(v1, 2);
 }
 
 // Eq. (rr), second half (after a grid barrier): Neumann k = M^{-1} r, l = M^{-1} s;
 // then w = A k, z = A l and the line-21 partials of the replaced vectors into P1.
-template <typename T>
-__device__ bool replace_r2(const SolverParams<T>& p, double* P1, double* smem, unsigned& epoch,
-                           int row0, int row1) {
+template <typename T, typename VR, typename Team>
+__device__ bool replace_r2(const SolverParams<T, VR>& p, Team& team) {
   using Acc = typename AccOf<T>::type;
+  const int row0 = team.row0, row1 = team.row1;
   const bool neu = p.prec == 2;
-  if (neu && !neumann_apply(p, p.r, p.k, p.s, p.l, epoch, row0, row1)) return false;
+  if (neu && !neumann_apply(p, team, p.r, p.k, p.s, p.l)) return false;
   Acc a_rr, a_rw, a_rs, a_rz, a_r2;
   for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
     const T wi = neu ? row_dot<T>(p.Au, p.k, i) : row_dot<T>(p.At, p.r, i);
@@ -152,27 +196,22 @@ __device__ bool replace_r2(const SolverParams<T>& p, double* P1, double* smem, u
     a_rr.add(rh, ri); a_rw.add(rh, wi); a_rs.add(rh, si); a_rz.add(rh, zi); a_r2.add(ri, ri);
   }
   double v5[5] = {a_rr.value(), a_rw.value(), a_rs.value(), a_rz.value(), a_r2.value()};
-  block_publish<5>(v5, smem, P1);
+  team.template publish<5>(v5, 1);
   return true;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverParams<T> p) {
+// The whole solve (Algorithm 2 + Eq. rr) for one system, executed by a team.
+template <typename T, typename VR, typename Team>
+__device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   using Acc = typename AccOf<T>::type;
-  __shared__ double smem[32 * kMaxDots];
   const int n = p.n;
-  const int row0 = (int)min((long long)n, (long long)blockIdx.x * p.chunk);
-  const int row1 = min(n, row0 + p.chunk);
+  const int row0 = team.row0, row1 = team.row1;
   const bool neu = p.prec == 2;
-  unsigned epoch = 0;
-  double* P0 = p.part;
-  double* P1 = p.part + gridDim.x * kMaxDots;
-  double* P2 = p.part + 2 * gridDim.x * kMaxDots;
-  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  const bool leader = team.leader();
   int nrep = 0;
 
 #define PBCG_SYNC() \
-  do { if (!grid_barrier(p.bar, ++epoch, p.err, p.timeout_ns)) return; } while (0)
+  do { if (!team.sync()) return; } while (0)
 #define PBCG_ROWS for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x)
 #define PBCG_FINISH(st, its, rnv)                                                        \
   do {                                                                                   \
@@ -200,10 +239,10 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
       a_bb.add(bi, bi);
     }
     double v2[2] = {a_rr.value(), a_bb.value()};
-    block_publish<2>(v2, smem, P0);
+    team.template publish<2>(v2, 0);
   }
   PBCG_SYNC();
-  if (neu && !neumann_apply(p, p.r, p.k, (const T*)nullptr, (T*)nullptr, epoch, row0, row1)) return;
+  if (neu && !neumann_apply(p, team, p.r, p.k, (const T*)nullptr, (T*)nullptr)) return;
   {
     Acc a_rw;
     PBCG_ROWS {
@@ -212,15 +251,15 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
       a_rw.add(p.rh[i], wi);
     }
     double v1[1] = {a_rw.value()};
-    block_publish<1>(v1, smem, P1);
+    team.template publish<1>(v1, 1);
   }
   PBCG_SYNC();
   double rho, rw0, bn, rn;
   {
     double t2[2];
-    grid_combine<2>(P0, t2, smem);
+    team.template combine<2>(0, t2);
     double t1[1];
-    grid_combine<1>(P1, t1, smem);
+    team.template combine<1>(1, t1);
     rho = t2[0];
     bn = sqrt(t2[1]);
     rw0 = t1[0];
@@ -243,7 +282,7 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
 
   for (int it = 0; it < p.max_it; ++it) {
     // ---------------- m_i = M^{-1} w_i (Neumann only; on the fly otherwise)
-    if (neu && !neumann_apply(p, p.w, p.m, (const T*)nullptr, (T*)nullptr, epoch, row0, row1)) return;
+    if (neu && !neumann_apply(p, team, p.w, p.m, (const T*)nullptr, (T*)nullptr)) return;
     // ---------------- pass A: t_i = A m_i; lines 5-11; partials of line 12
     {
       const T aT = T(alpha), bT = T(beta), opT = T(omega_prev);
@@ -266,15 +305,15 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
         a_yy.add(y, y);
       }
       double v2[2] = {a_qy.value(), a_yy.value()};
-      block_publish<2>(v2, smem, P0);
+      team.template publish<2>(v2, 0);
     }
     PBCG_SYNC();
     // ---------------- n_i = M^{-1} z_i (Neumann only), overlapping the reduction
-    if (neu && !neumann_apply(p, p.z, p.nn, (const T*)nullptr, (T*)nullptr, epoch, row0, row1)) return;
+    if (neu && !neumann_apply(p, team, p.z, p.nn, (const T*)nullptr, (T*)nullptr)) return;
     double omega;
     {
       double t2[2];
-      grid_combine<2>(P0, t2, smem);
+      team.template combine<2>(0, t2);
       omega = t2[1] == 0.0 ? 0.0 : t2[0] / t2[1];     // line 16
     }
     if (!isfinite(omega)) PBCG_FINISH(kBreakdown, it, rn);
@@ -309,32 +348,32 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
       }
       if (!do_rr) {
         double v5[5] = {a_rr.value(), a_rw.value(), a_rs.value(), a_rz.value(), a_r2.value()};
-        block_publish<5>(v5, smem, P1);
+        team.template publish<5>(v5, 1);
       }
     }
     // ---------------- residual replacement, Eq. (rr), after line 20 (reading R6)
     if (do_rr) {
       PBCG_SYNC();
-      if (!replace_r1(p, nullptr, P2, smem, true, row0, row1)) return;
+      replace_r1(p, team, true);
       PBCG_SYNC();
-      if (!replace_r2(p, P1, smem, epoch, row0, row1)) return;
+      if (!replace_r2(p, team)) return;
       ++nrep;
     }
     rep_last = do_rr;
     PBCG_SYNC();
     // ---------------- lines 21-26: second reduction, stopping test, beta, alpha
     double t5[5];
-    grid_combine<5>(P1, t5, smem);
+    team.template combine<5>(1, t5);
     double rho_new = t5[0], rw = t5[1], rs = t5[2], rz = t5[3];
     rn = sqrt(t5[4]);
     if (rn <= p.tol * bn) {
       // reading R5: verify with the FP64 true residual; with a replacement policy a
       // failed check forces a replacement, without one the solve has stagnated.
       const bool any_rr = p.rr_period > 0 || p.rr_theta > 0.0;
-      if (!replace_r1(p, nullptr, P2, smem, any_rr, row0, row1)) return;
+      replace_r1(p, team, any_rr);
       PBCG_SYNC();
       double t1[1];
-      grid_combine<1>(P2, t1, smem);
+      team.template combine<1>(2, t1);
       const double true_rn = sqrt(t1[0]);
       if (leader) p.res->true_rel = true_rn / bn;
       if (true_rn <= p.tol * bn || !any_rr) {
@@ -344,12 +383,12 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
         }
         PBCG_FINISH(true_rn <= p.tol * bn ? kOK : kStagnated, it + 1, rn);
       }
-      if (!replace_r2(p, P1, smem, epoch, row0, row1)) return;
+      if (!replace_r2(p, team)) return;
       ++nrep;
       rep_last = true;
       do_rr = true;
       PBCG_SYNC();
-      grid_combine<5>(P1, t5, smem);
+      team.template combine<5>(1, t5);
       rho_new = t5[0]; rw = t5[1]; rs = t5[2]; rz = t5[3];
       rn = sqrt(t5[4]);
     }
@@ -372,6 +411,22 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
 #undef PBCG_SYNC
 #undef PBCG_ROWS
 #undef PBCG_FINISH
+}
+
+// One cooperative grid solves one system; block b owns rows [b*chunk, (b+1)*chunk).
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverParams<T> p) {
+  __shared__ double smem[32 * 8 + 3 * kMaxDots];
+  GridTeam team;
+  team.row0 = (int)min((long long)p.n, (long long)blockIdx.x * p.chunk);
+  team.row1 = min(p.n, team.row0 + p.chunk);
+  team.epoch = 0;
+  team.bar = p.bar;
+  team.err = p.err;
+  team.timeout_ns = p.timeout_ns;
+  team.part = p.part;
+  team.smem = smem;
+  solve_body(p, team);
 }
 
 }  // namespace pbcg

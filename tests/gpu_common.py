@@ -69,3 +69,22 @@ def iterate_tolerance(sens, floor=1e-10, factor=100.0):
     """max(1e-10, 100 * s_i): the stated 1e-10 wherever the problem's own rounding
     sensitivity allows it, else two orders of magnitude above that sensitivity."""
     return np.maximum(floor, factor * sens)
+
+
+def oracle_iteration_spread(A, b, **kw):
+    """Iterations the oracle needs under three dot-product summation orders (BLAS, exactly
+    rounded fsum, reversed index order).  On the convection-diffusion operators the
+    convergence history is sensitive enough that these differ (e.g. 192 vs 357 on a
+    97x97 grid), so an independent implementation is compared against this range."""
+    orig = krylov._dot
+    orders = [orig,
+              lambda u, v: math.fsum(u.astype(np.float64) * v.astype(np.float64)),
+              lambda u, v: float(np.dot(u[::-1].astype(np.float64), v[::-1].astype(np.float64)))]
+    out = []
+    try:
+        for f in orders:
+            krylov._dot = f
+            out.append(oracle.pbicgstab(A, b, **kw))
+    finally:
+        krylov._dot = orig
+    return out

@@ -1,0 +1,81 @@
+"""Batched solver (one persistent launch, one block per system) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import testproblems as tp
+from gpu_common import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch_solver(bp, **kw):
+    torch = torch_cuda()
+    import paper_1809_01948_gb300 as pb
+    c = bp.concat()
+    dev = torch.device("cuda:0")
+    s = pb.BatchSolver(c["row_off"], c["nnz_off"], torch.from_numpy(c["row_ptr"]).to(dev),
+                       torch.from_numpy(c["col"]).to(dev), torch.from_numpy(c["val"]).to(dev), **kw)
+    return s, c, torch.from_numpy(c["b"]).to(dev)
+
+
+def test_batched_small_uneven_matches_oracle():
+    bp = tp.config4(nsys=24, n_lo=50, n_hi=3000, band=64)
+    s, c, b = _batch_solver(bp, precision="mixed", tol=1e-8, max_it=500, rr_theta=1e-3)
+    x, info = s.solve(b)
+    x = x.cpu().numpy()
+    assert info["n_ok"] == 24, info["status"]
+    for k, sysk in enumerate(bp.systems):
+        xk = x[c["row_off"][k]:c["row_off"][k + 1]]
+        A = sysk.A.to_scipy(np.float64)
+        true = np.linalg.norm(sysk.b - A @ xk) / np.linalg.norm(sysk.b)
+        assert true <= 1e-8 and abs(true - info["rel_res_true"][k]) <= 1e-3 * true + 1e-18
+        ref = oracle.pbicgstab(A, sysk.b, precond="jacobi", tol=1e-8, maxit=500, mixed=True, rr_theta=1e-3)
+        assert ref.status == oracle.Status.OK
+        # mixed mode: replacement points depend on FP32 rounding, so only an upper bound
+        assert int(info["iterations"][k]) <= 1.5 * ref.iterations + 5
+
+
+def test_batched_fp64_iterates_equal_single_solver():
+    """FP64 batched solves give the same answers as the single-system solver."""
+    torch = torch_cuda()
+    from gpu_common import make_solver, gpu_solve
+    bp = tp.config4(nsys=5, n_lo=500, n_hi=2000, band=40)
+    s, c, b = _batch_solver(bp, precision="fp64", tol=1e-12, max_it=500, rr_period=50)
+    x, info = s.solve(b)
+    x = x.cpu().numpy()
+    assert info["n_ok"] == 5
+    for k, sysk in enumerate(bp.systems):
+        single = make_solver(tp.Problem("s", sysk.A, sysk.b, sysk.x0, None, precond="jacobi", fmt="csr"),
+                             tol=1e-12, max_it=500, rr_period=50)
+        xs, res, _, _ = gpu_solve(single, sysk.b)
+        xk = x[c["row_off"][k]:c["row_off"][k + 1]]
+        assert res.status == 0
+        assert np.linalg.norm(xk - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+def test_batched_graph_replay_and_autotune():
+    bp = tp.config4(nsys=40, n_lo=100, n_hi=5000, band=128)
+    s, c, b = _batch_solver(bp, precision="mixed", tol=1e-8, max_it=500, rr_theta=1e-3)
+    x1, i1 = s.solve(b)
+    x1 = x1.clone()
+    x2, i2 = s.solve(b, x1.new_zeros(x1.shape))
+    assert i1["n_ok"] == 40 and i2["n_ok"] == 40
+    assert i1["block_threads"] in (256, 512, 1024) and i1["grid_blocks"] > 0
+    assert np.array_equal(i1["iterations"], i2["iterations"])
+    # same launch shape and inputs: bitwise identical solution
+    assert bool((x1 == x2).all())
+
+
+def test_batched_invalid_input_rejected():
+    torch = torch_cuda()
+    import paper_1809_01948_gb300 as pb
+    dev = torch.device("cuda:0")
+    row_off = np.array([0, 2], np.int64)
+    nnz_off = np.array([0, 2], np.int64)
+    rp = torch.tensor([0, 1, 2], dtype=torch.int32, device=dev)
+    col = torch.tensor([0, 7], dtype=torch.int32, device=dev)        # column out of range
+    val = torch.ones(2, dtype=torch.float32, device=dev)
+    with pytest.raises(pb.PBCGError) as e:
+        pb.BatchSolver(row_off, nnz_off, rp, col, val)
+    assert e.value.status == 1
