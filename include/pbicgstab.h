@@ -224,6 +224,42 @@ pbcg_status pbicgstab_batch_destroy(pbcg_batch_ctx* ctx);
 pbcg_status pbicgstab_solve_batched(const pbcg_batch* batch, const pbcg_options* opt, void* stream,
                                     const double* b, double* x, pbcg_batch_result* res);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free solve.  The paper has no counterpart: this entry point exists
+ * for callers that must not allocate GPU memory -- for example an application
+ * whose own allocator has reserved the device memory up front (a cudaMalloc from
+ * this library would then fail), or a latency-critical loop that cannot afford
+ * the implicit device synchronisation of cudaMalloc/cudaFree.
+ *
+ * It runs the same persistent FP64 solver kernel as pbicgstab_solve (Algorithm 2
+ * with the Eq. (rr) policies of *opt), but every scratch buffer (15 work vectors,
+ * D^{-1}, the operator A D^{-1}, reduction partials, barrier and result state)
+ * lives in one fixed array of device memory that the library declares
+ * statically.  That array is reserved on every GPU that loads the library, for
+ * as long as the process runs: about 8.6 MB.  The call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine) and keeps no reference to
+ * the caller's arrays after it returns.
+ *
+ * Limits: n <= PBCG_NOALLOC_MAX_N rows and at most PBCG_NOALLOC_MAX_VALUES stored
+ * values (CSR nnz, or ndiag * n for DIA); FP64 values (val_dtype PBCG_F64) and
+ * opt->precision == PBCG_FP64; preconditioner NONE or JACOBI.  Larger systems or
+ * other settings return PBCG_INVALID_ARG with a message naming the limit.
+ *
+ * A: device CSR or DIA matrix (DIA offsets on the host), used in place.
+ * b: device, read.  x: device, read as x0 and overwritten.  res: host, filled
+ * (time_ms is -1: no events are created).  The call waits for the solve.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls on a device share the one array and it keeps
+ * the last call's contents (the solver re-initialises what must start at zero):
+ * calls that overlap on the GPU -- from several host threads or streams at
+ * once -- race on it and must be serialised by the caller. */
+#define PBCG_NOALLOC_MAX_N 32768
+#define PBCG_NOALLOC_MAX_VALUES 524288
+pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_precond* M, const pbcg_options* opt,
+                                    const double* b, double* x, pbcg_result* res, void* stream);
+
 /* Test hook for the fault-detection path: launches a cooperative grid whose
  * blocks wait at a barrier for `extra_arrivals` more blocks than exist, so the
  * wait can only end by its timeout.  Returns PBCG_OK when the kernel gave up

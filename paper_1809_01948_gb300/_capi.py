@@ -16,6 +16,8 @@ F64, F32 = 0, 1
 PREC_NONE, PREC_JACOBI, PREC_NEUMANN = 0, 1, 2
 FP64, MIXED = 0, 1
 HIST_STRIDE = 8
+NOALLOC_MAX_N = 32768
+NOALLOC_MAX_VALUES = 524288
 
 
 class Matrix(C.Structure):
@@ -72,6 +74,8 @@ PROTOTYPES = {
     "pbicgstab_destroy": (C.c_int, [C.c_void_p]),
     "pbicgstab_last_error": (C.c_char_p, []),
     "pbicgstab_test_barrier_timeout": (C.c_int, [C.c_double, C.c_int32, C.POINTER(C.c_int32)]),
+    "pbicgstab_solve_noalloc": (C.c_int, [C.POINTER(Matrix), C.POINTER(Precond), C.POINTER(Options), C.c_void_p,
+                                          C.c_void_p, C.POINTER(Result), C.c_void_p]),
     "pbicgstab_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Batch), C.POINTER(Options), C.c_void_p]),
     "pbicgstab_batch_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BatchResult)]),
     "pbicgstab_batch_destroy": (C.c_int, [C.c_void_p]),
