@@ -56,6 +56,7 @@ __device__ __forceinline__ MatView<V> csr_view(int n, const int* rp, const int* 
 template <typename T, typename VR>
 __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchDev d) {
   __shared__ double smem[32 * 8 + 3 * kMaxDots];
+  __shared__ double scal[8];
   __shared__ int s_sys;
   for (;;) {
     __syncthreads();
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchDev d) 
     team.row0 = 0;
     team.row1 = n;
     team.smem = smem;
+    team.scal = scal;
     solve_body(p, team);
     __syncthreads();
     // final FP64 true residual of this system

@@ -80,6 +80,7 @@ struct GridTeam {
   unsigned long long timeout_ns;
   double* part;
   double* smem;   // >= 32*8 + kMaxDots doubles
+  double* scal;   // >= 8 doubles of shared memory for scalar broadcasts
   __device__ __forceinline__ bool sync() { return grid_barrier(bar, ++epoch, err, timeout_ns); }
   template <int ND>
   __device__ __forceinline__ void publish(double (&v)[ND], int set) {
@@ -95,6 +96,7 @@ struct GridTeam {
 struct BlockTeam {
   int row0, row1;
   double* smem;   // >= 32*8 + 3*kMaxDots doubles
+  double* scal;   // >= 8 doubles of shared memory for scalar broadcasts
   __device__ __forceinline__ bool sync() { __syncthreads(); return true; }
   template <int ND>
   __device__ __forceinline__ void publish(double (&v)[ND], int set) {
@@ -213,6 +215,14 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
 #define PBCG_SYNC() \
   do { if (!team.sync()) return; } while (0)
 #define PBCG_ROWS for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x)
+  // FP64 division and square root are multi-instruction sequences on the scarce FP64
+  // pipe: thread 0 evaluates them and the block reads the results from shared memory.
+  double* const sc = team.scal;
+#define PBCG_BCAST_BEGIN if (threadIdx.x == 0) {
+#define PBCG_BCAST_END \
+  }                    \
+  __syncthreads();
+#define PBCG_BCAST_DONE __syncthreads();
 #define PBCG_FINISH(st, its, rnv)                                                        \
   do {                                                                                   \
     if (leader) {                                                                        \
@@ -254,16 +264,25 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     team.template publish<1>(v1, 1);
   }
   PBCG_SYNC();
-  double rho, rw0, bn, rn;
+  double rho, rw0, bn, rn, alpha, tolb;
   {
     double t2[2];
     team.template combine<2>(0, t2);
     double t1[1];
     team.template combine<1>(1, t1);
     rho = t2[0];
-    bn = sqrt(t2[1]);
     rw0 = t1[0];
-    rn = sqrt(rho);
+    PBCG_BCAST_BEGIN
+      sc[0] = sqrt(t2[1]);
+      sc[1] = sqrt(rho);
+      sc[2] = rw0 != 0.0 ? rho / rw0 : INFINITY;
+      sc[3] = p.tol * sc[0];
+    PBCG_BCAST_END
+    bn = sc[0];
+    rn = sc[1];
+    alpha = sc[2];
+    tolb = sc[3];
+    PBCG_BCAST_DONE
   }
   if (leader) { p.res->bnorm = bn; p.res->rn0 = rn; p.res->true_rel = -1.0; }
   if (bn == 0.0) {            // b = 0: x = 0
@@ -271,14 +290,14 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     if (leader) { p.res->status = kOK; p.res->iterations = 0; p.res->nrep = 0; p.res->rn_rel = 0.0; }
     return;
   }
-  if (rn <= p.tol * bn) PBCG_FINISH(kOK, 0, rn);
-  double alpha = rw0 != 0.0 ? rho / rw0 : INFINITY;
+  if (rn <= tolb) PBCG_FINISH(kOK, 0, rn);
   if (rw0 == 0.0 || !isfinite(alpha)) PBCG_FINISH(kBreakdown, 0, rn);
   double beta = 0.0, omega_prev = 0.0;
   const double rn0 = rn;
-  double rn_last_rr = rn;
   bool rep_last = false;
   const double sqrt_eps = 1.4901161193847656e-08;  // sqrt(2^-52)
+  const double rr_cutoff = sqrt_eps * rn0;          // periodic replacements stop below this
+  double rr_theta_thr = p.rr_theta * rn;            // relative trigger threshold
 
   for (int it = 0; it < p.max_it; ++it) {
     // ---------------- m_i = M^{-1} w_i (Neumann only; on the fly otherwise)
@@ -314,12 +333,16 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     {
       double t2[2];
       team.template combine<2>(0, t2);
-      omega = t2[1] == 0.0 ? 0.0 : t2[0] / t2[1];     // line 16
+      PBCG_BCAST_BEGIN
+        sc[0] = t2[1] == 0.0 ? 0.0 : t2[0] / t2[1];   // line 16
+      PBCG_BCAST_END
+      omega = sc[0];
+      PBCG_BCAST_DONE
     }
     if (!isfinite(omega)) PBCG_FINISH(kBreakdown, it, rn);
     bool do_rr = false;
-    if (p.rr_period > 0 && it > 0 && it % p.rr_period == 0 && rn >= sqrt_eps * rn0) do_rr = true;
-    if (p.rr_theta > 0.0 && rn <= p.rr_theta * rn_last_rr) do_rr = true;
+    if (p.rr_period > 0 && it > 0 && it % p.rr_period == 0 && rn >= rr_cutoff) do_rr = true;
+    if (p.rr_theta > 0.0 && rn <= rr_theta_thr) do_rr = true;
     // ---------------- pass B: v_i = A n_i; lines 17-20; partials of line 21
     {
       const T aT = T(alpha), oT = T(omega);
@@ -365,8 +388,12 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     double t5[5];
     team.template combine<5>(1, t5);
     double rho_new = t5[0], rw = t5[1], rs = t5[2], rz = t5[3];
-    rn = sqrt(t5[4]);
-    if (rn <= p.tol * bn) {
+    PBCG_BCAST_BEGIN
+      sc[0] = sqrt(t5[4]);
+    PBCG_BCAST_END
+    rn = sc[0];
+    PBCG_BCAST_DONE
+    if (rn <= tolb) {
       // reading R5: verify with the FP64 true residual; with a replacement policy a
       // failed check forces a replacement, without one the solve has stagnated.
       const bool any_rr = p.rr_period > 0 || p.rr_theta > 0.0;
@@ -374,14 +401,18 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       PBCG_SYNC();
       double t1[1];
       team.template combine<1>(2, t1);
-      const double true_rn = sqrt(t1[0]);
-      if (leader) p.res->true_rel = true_rn / bn;
-      if (true_rn <= p.tol * bn || !any_rr) {
+      PBCG_BCAST_BEGIN
+        sc[0] = sqrt(t1[0]);
+        p.res->true_rel = sc[0] / bn;
+      PBCG_BCAST_END
+      const double true_rn = sc[0];
+      PBCG_BCAST_DONE
+      if (true_rn <= tolb || !any_rr) {
         if (leader && it < p.hist_len) {
           double* h = p.hist_s + (size_t)it * PBCG_HS;
           h[0] = alpha; h[1] = omega; h[2] = NAN; h[3] = rn / bn; h[4] = do_rr ? 1.0 : 0.0;
         }
-        PBCG_FINISH(true_rn <= p.tol * bn ? kOK : kStagnated, it + 1, rn);
+        PBCG_FINISH(true_rn <= tolb ? kOK : kStagnated, it + 1, rn);
       }
       if (!replace_r2(p, team)) return;
       ++nrep;
@@ -390,13 +421,25 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       PBCG_SYNC();
       team.template combine<5>(1, t5);
       rho_new = t5[0]; rw = t5[1]; rs = t5[2]; rz = t5[3];
-      rn = sqrt(t5[4]);
+      PBCG_BCAST_BEGIN
+        sc[0] = sqrt(t5[4]);
+      PBCG_BCAST_END
+      rn = sc[0];
+      PBCG_BCAST_DONE
     }
-    if (do_rr) rn_last_rr = rn;
+    double beta_new, alpha_new, den;
+    PBCG_BCAST_BEGIN
+      if (do_rr) sc[3] = p.rr_theta * rn;
+      sc[0] = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_new, rho));                               // line 25
+      sc[1] = __dsub_rn(__dadd_rn(rw, __dmul_rn(sc[0], rs)), __dmul_rn(__dmul_rn(sc[0], omega), rz));   // line 26
+      sc[2] = sc[1] != 0.0 ? __ddiv_rn(rho_new, sc[1]) : INFINITY;
+    PBCG_BCAST_END
+    beta_new = sc[0];
+    den = sc[1];
+    alpha_new = sc[2];
+    if (do_rr) rr_theta_thr = sc[3];
+    PBCG_BCAST_DONE
     if (omega == 0.0 || rho == 0.0) PBCG_FINISH(kBreakdown, it + 1, rn);
-    const double beta_new = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_new, rho));          // line 25
-    const double den = __dsub_rn(__dadd_rn(rw, __dmul_rn(beta_new, rs)), __dmul_rn(__dmul_rn(beta_new, omega), rz));
-    const double alpha_new = den != 0.0 ? __ddiv_rn(rho_new, den) : INFINITY;                       // line 26
     if (leader && it < p.hist_len) {
       double* h = p.hist_s + (size_t)it * PBCG_HS;
       h[0] = alpha; h[1] = omega; h[2] = beta_new; h[3] = rn / bn; h[4] = do_rr ? 1.0 : 0.0;
@@ -411,12 +454,16 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
 #undef PBCG_SYNC
 #undef PBCG_ROWS
 #undef PBCG_FINISH
+#undef PBCG_BCAST_BEGIN
+#undef PBCG_BCAST_END
+#undef PBCG_BCAST_DONE
 }
 
 // One cooperative grid solves one system; block b owns rows [b*chunk, (b+1)*chunk).
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverParams<T> p) {
   __shared__ double smem[32 * 8 + 3 * kMaxDots];
+  __shared__ double scal[8];
   GridTeam team;
   team.row0 = (int)min((long long)p.n, (long long)blockIdx.x * p.chunk);
   team.row1 = min(p.n, team.row0 + p.chunk);
@@ -426,6 +473,7 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
   team.timeout_ns = p.timeout_ns;
   team.part = p.part;
   team.smem = smem;
+  team.scal = scal;
   solve_body(p, team);
 }
 
