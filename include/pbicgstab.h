@@ -102,13 +102,19 @@ typedef struct pbcg_options {
   double* hist_scalars;    /* device, hist_len*PBCG_HIST_STRIDE doubles, or NULL      */
   int32_t grid_blocks;     /* persistent grid size; 0 = automatic                     */
   int32_t block_threads;   /* threads per block (multiple of 32, <= 1024); 0 = auto   */
+  int32_t max_restarts;    /* after a breakdown (zero or non-finite omega, (r0,r_i),
+                              beta or alpha denominator) restart Algorithm 2 from the
+                              current iterate with a new shadow vector, at most this many
+                              times (0, the default, = the paper's algorithm: report
+                              PBCG_BREAKDOWN)                                          */
+  int32_t reserved1;
 } pbcg_options;
 
 typedef struct pbcg_result {
   int32_t status;          /* pbcg_status of the solve */
   int32_t iterations;      /* completed iterations of Algorithm 2 */
   int32_t n_replacements;  /* executed Eq. (rr) steps (periodic, relative and forced) */
-  int32_t reserved0;
+  int32_t n_restarts;      /* restarts after breakdowns (options.max_restarts) */
   double rel_res_recursive;/* ||r_last|| / ||b|| (recursively computed residual) */
   double rel_res_true;     /* ||b - A x|| / ||b||, FP64 */
   double time_ms;          /* device time of the persistent solver kernel (CUDA events
@@ -117,8 +123,8 @@ typedef struct pbcg_result {
 
 typedef struct pbcg_ctx pbcg_ctx;
 
-/* Fill *opt with defaults: FP64, max_it 10000, tol 1e-10, no replacement,
- * timeout 2000 ms, no history, automatic launch shape.  opt: host, non-NULL. */
+/* Fill *opt with defaults: FP64, max_it 10000, tol 1e-10, no replacement, no
+ * restarts, timeout 2000 ms, no history, automatic launch shape.  opt: host, non-NULL. */
 pbcg_status pbicgstab_default_options(pbcg_options* opt);
 
 /* Create a solver context for A and M^{-1} (Algorithm 2's inputs other than b,
@@ -148,6 +154,30 @@ pbcg_status pbicgstab_solve(pbcg_ctx* ctx, const double* b, double* x, pbcg_resu
  * enqueued on the context's stream and waited for.  res: host, non-NULL. */
 pbcg_status pbicgstab_solve_host(pbcg_ctx* ctx, const double* b_host, double* x_host,
                                  pbcg_result* res);
+
+/* Solve A X = B for nrhs right-hand sides with one matrix (Algorithm 2 + Eq. rr for
+ * each column independently: its own alpha, beta, omega, replacements and stop).
+ * B, X: device, column-major n x nrhs (column c at offset c*n); X is read as the
+ * initial guesses and overwritten.  The grid is split into teams of blocks, one
+ * team per right-hand side, each with its own barrier and reductions; more than
+ * (co-resident blocks) right-hand sides run in waves.  res: host array of nrhs
+ * results or NULL; time_ms of every entry is the total kernel time.  Waits.
+ * Returns PBCG_OK when every column converged, else the first failing status. */
+pbcg_status pbicgstab_solve_multi(pbcg_ctx* ctx, int32_t nrhs, const double* B, double* X,
+                                  pbcg_result* res);
+
+/* Create a context for the transposed matrix A^T (CSR only) with the same
+ * preconditioner kind and options: the adjoint solve A^T lambda = dL/dx of a
+ * differentiable solve.  A^T is built on the device (column counts, scan,
+ * scatter, and a per-row sort that makes it independent of atomic order). */
+pbcg_status pbicgstab_create_transpose(pbcg_ctx** out, const pbcg_ctx* src);
+
+/* Gradient of a loss with respect to the stored CSR values of the context's
+ * matrix, given the adjoint solutions Lam (A^T Lam = dL/dX) and the solutions X
+ * (device, column-major n x nrhs):  grad[e] = - sum_c Lam[row_e, c] X[col_e, c]
+ * for every stored entry e in CSR order (device, nnz doubles).  Stream-ordered. */
+pbcg_status pbicgstab_csr_value_grad(pbcg_ctx* ctx, int32_t nrhs, const double* Lam, const double* X,
+                                     double* grad);
 
 /* y = A x with the context's FP64 matrix (x, y: device, n doubles). */
 pbcg_status pbicgstab_spmv(pbcg_ctx* ctx, const double* x, double* y);

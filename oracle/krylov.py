@@ -36,6 +36,9 @@ R8  Mixed mode adds a relative trigger: replace when ||r_i|| <= theta * (the
 R15 Breakdown: a zero or non-finite alpha denominator, omega, (r_hat, r_i) or
     beta returns BREAKDOWN with the last finite x.  (y, y) == 0 sets omega = 0
     (y = 0 only when q = 0 in exact arithmetic), so the stop test decides.
+    With max_restarts > 0 (not in the paper) a breakdown instead restarts lines 2-3
+    from the current iterate, with the new residual as the shadow vector; the
+    iteration in which the breakdown was found counts as completed.
 
 Mixed emulation (``mixed=True``): every vector except x and b is stored in
 FP32 and every vector operation is evaluated in FP32 with the FP32-rounded
@@ -86,6 +89,7 @@ class SolveResult:
     replaced: List[bool] = field(default_factory=list)
     fr: List[float] = field(default_factory=list)            # gap bound f^r_{i+1} (auto policy)
     xs: List[np.ndarray] = field(default_factory=list)       # x_{i+1}, first `record` iterations
+    n_restarts: int = 0
 
 
 def _as_scipy(A):
@@ -191,7 +195,8 @@ def bicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float =
 def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float = 1e-10,
               maxit: int = 1000, rr_period: int = 0, rr_theta: float = 0.0, rr_auto: bool = False,
               rr_tau: Optional[float] = None, mixed: bool = False, record: int = 0,
-              observer: Optional[Callable] = None, track_bound: bool = False) -> SolveResult:
+              observer: Optional[Callable] = None, track_bound: bool = False,
+              max_restarts: int = 0) -> SolveResult:
     """Algorithm 2 of the paper (lines cited as "l.N"), plus Eq. (rr) replacements.
 
     Replacement policies (any combination; all off means plain p-BiCGStab):
@@ -218,142 +223,171 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
         return res
     sc = (lambda a: T(a))                     # scalar in the vector precision
 
-    # l.2-3: initialisation
-    r = (b - A64 @ x).astype(T)
-    rhat = r.copy()
-    k = M.apply(r)
-    w = AT @ k
-    m = M.apply(w)
-    t = AT @ m
-    rho = _dot(rhat, r)
-    rw = _dot(rhat, w)
-    rn = math.sqrt(_dot(r, r))
-    rn0 = rn
-    if rn <= tol * bnorm:
-        res.status, res.rel_res_recursive, res.rel_res_true = Status.OK, rn / bnorm, rn / bnorm
-        return res
-    alpha = rho / rw if rw != 0.0 else math.inf
-    if rw == 0.0 or not math.isfinite(alpha):
-        res.status = Status.BREAKDOWN
-        res.rel_res_recursive = res.rel_res_true = rn / bnorm
-        return res
-    beta = 0.0
-    omega_prev = 0.0
-    zero = np.zeros(n, dtype=T)
-    g, s, l, z, nv, v = zero, zero, zero, zero, zero, zero   # reading R3
-    rn_last_rr = rn0
+    it = 0
+    n_restarts = 0
+    first = True
+    rn0 = 0.0
     eps = EPS64
     tau = math.sqrt(eps) if rr_tau is None else rr_tau
     fbound = _GapBound(A64, M, b, eps, mixed) if (rr_auto or track_bound) else None
-    if fbound is not None:
-        fbound.start(x, rn)
-
-    def replace(x_, g_):
-        """Eq. (rr): r = b - A x, k = M^{-1} r, w = A k, s = A g, l = M^{-1} s, z = A l."""
-        r_ = (b - A64 @ x_).astype(T)
-        k_ = M.apply(r_)
-        w_ = AT @ k_
-        s_ = (A64 @ g_.astype(np.float64)).astype(T)
-        l_ = M.apply(s_)
-        z_ = AT @ l_
-        return r_, k_, w_, s_, l_, z_
-
-    if observer is not None:
-        observer("init", -1, dict(x=x, r=r, k=k, w=w, m=m, t=t))
-    fr_hist = [fbound.f] if fbound is not None else None   # f^r_i, i = 0, 1, ...
-    rn_hist = [rn]                                          # ||r_i||
-    for i in range(maxit):
-        a_, b_, wp_ = sc(alpha), sc(beta), sc(omega_prev)
-        g_prev, l_prev, s_prev, z_prev, n_prev, v_prev = g, l, s, z, nv, v
-        g = k + b_ * (g - wp_ * l)          # l.5
-        s = w + b_ * (s - wp_ * z)          # l.6
-        l = m + b_ * (l - wp_ * nv)         # l.7
-        z = t + b_ * (z - wp_ * v)          # l.8
-        q = r - a_ * s                      # l.9
-        u = k - a_ * l                      # l.10
-        y = w - a_ * z                      # l.11
-        qy, yy = _dot(q, y), _dot(y, y)     # l.12
-        nv = M.apply(z)                     # l.13
-        v = AT @ nv                         # l.14
-        omega = 0.0 if yy == 0.0 else qy / yy   # l.16
-        if not math.isfinite(omega):
+    while True:                             # restarts after breakdowns (max_restarts)
+        # l.2-3: initialisation
+        r = (b - A64 @ x).astype(T)
+        rhat = r.copy()
+        k = M.apply(r)
+        w = AT @ k
+        m = M.apply(w)
+        t = AT @ m
+        rho = _dot(rhat, r)
+        rw = _dot(rhat, w)
+        rn = math.sqrt(_dot(r, r))
+        if first:
+            rn0 = rn
+        if rn <= tol * bnorm:
+            res.status, res.rel_res_recursive = Status.OK, rn / bnorm
+            res.x, res.rel_res_true, res.iterations = x, _true_res(A64, b, x) / bnorm, it
+            return res
+        alpha = rho / rw if rw != 0.0 else math.inf
+        if rw == 0.0 or not math.isfinite(alpha):
             res.status = Status.BREAKDOWN
-            break
-        o_ = sc(omega)
-        # replacement decision for this iteration (uses only quantities known now)
-        do_rr = False
-        if rr_period > 0 and i > 0 and i % rr_period == 0 and rn >= math.sqrt(eps) * rn0:
-            do_rr = True                                             # reading R7
-        if rr_theta > 0 and rn <= rr_theta * rn_last_rr:
-            do_rr = True                                             # reading R8
-        if rr_auto and i > 0 and (fr_hist[i - 1] <= tau * rn_hist[i - 1] and fr_hist[i] > tau * rn_hist[i]):
-            do_rr = True                                             # Eq. (criterion)
-        x_old = x
-        x = (x + alpha * g.astype(np.float64)) + omega * u.astype(np.float64)   # l.17
-        r_new = q - o_ * y                  # l.18
-        k_new = u - o_ * (m - a_ * nv)      # l.19
-        w_new = y - o_ * (t - a_ * v)       # l.20
+            res.x, res.rel_res_recursive, res.rel_res_true = x, rn / bnorm, _true_res(A64, b, x) / bnorm
+            return res
+        beta = 0.0
+        omega_prev = 0.0
+        zero = np.zeros(n, dtype=T)
+        g, s, l, z, nv, v = zero, zero, zero, zero, zero, zero   # reading R3
+        rn_last_rr = rn
+        if fbound is not None:
+            fbound.start(x, rn)
+        first = False
+        restart = False
+
+        def replace(x_, g_):
+            """Eq. (rr): r = b - A x, k = M^{-1} r, w = A k, s = A g, l = M^{-1} s, z = A l."""
+            r_ = (b - A64 @ x_).astype(T)
+            k_ = M.apply(r_)
+            w_ = AT @ k_
+            s_ = (A64 @ g_.astype(np.float64)).astype(T)
+            l_ = M.apply(s_)
+            z_ = AT @ l_
+            return r_, k_, w_, s_, l_, z_
+
         if observer is not None:
-            observer("iter", i, dict(x=x_old, x_new=x, r=r, k=k, w=w, g=g, s=s, l=l, z=z, q=q, u=u,
-                                     y=y, m=m, t=t, n=nv, v=v, r_new=r_new, k_new=k_new,
-                                     w_new=w_new, g_prev=g_prev, l_prev=l_prev, s_prev=s_prev,
-                                     z_prev=z_prev, n_prev=n_prev, v_prev=v_prev, alpha=alpha,
-                                     beta=beta, omega=omega, omega_prev=omega_prev, replaced=do_rr))
-        if fbound is not None:
-            fbound.step(alpha, beta, omega, omega_prev, x_old, r, k, w, g, s, l, z, q, u, y, m, t, nv, v)
-        r, k, w = r_new, k_new, w_new
-        if do_rr:                           # Eq. (rr), after l.20 (reading R6)
-            r, k, w, s, l, z = replace(x, g)
-            res.n_replacements += 1
-            if observer is not None:
-                observer("replace", i, dict(x=x, r=r, k=k, w=w, g=g, s=s, l=l, z=z))
-            if fbound is not None:
-                fbound.reset(x, k, g, s, l, z)
-        # l.21-24: second global reduction, overlapped with m = M^{-1} w, t = A m
-        rho_new, rw, rs, rz = _dot(rhat, r), _dot(rhat, w), _dot(rhat, s), _dot(rhat, z)
-        rr = _dot(r, r)
-        m = M.apply(w)                      # l.22
-        t = AT @ m                          # l.23
-        res.iterations = i + 1
-        rn = math.sqrt(rr)
-        if rn <= tol * bnorm:               # reading R5
-            tr = _true_res(A64, b, x)
-            if tr <= tol * bnorm:
-                res.status = Status.OK
-                _log(res, alpha, omega, None, rn, do_rr, x, i, record, fbound)
+            observer("init", -1, dict(x=x, r=r, k=k, w=w, m=m, t=t))
+        fr_hist = [fbound.f] if fbound is not None else None   # f^r_i, i = 0, 1, ...
+        rn_hist = [rn]                                          # ||r_i||
+        while it < maxit:
+            i = it
+            a_, b_, wp_ = sc(alpha), sc(beta), sc(omega_prev)
+            g_prev, l_prev, s_prev, z_prev, n_prev, v_prev = g, l, s, z, nv, v
+            g = k + b_ * (g - wp_ * l)          # l.5
+            s = w + b_ * (s - wp_ * z)          # l.6
+            l = m + b_ * (l - wp_ * nv)         # l.7
+            z = t + b_ * (z - wp_ * v)          # l.8
+            q = r - a_ * s                      # l.9
+            u = k - a_ * l                      # l.10
+            y = w - a_ * z                      # l.11
+            qy, yy = _dot(q, y), _dot(y, y)     # l.12
+            nv = M.apply(z)                     # l.13
+            v = AT @ nv                         # l.14
+            omega = 0.0 if yy == 0.0 else qy / yy   # l.16
+            if not math.isfinite(omega):
+                if n_restarts < max_restarts:
+                    n_restarts += 1
+                    it += 1
+                    restart = True
+                    break
+                res.status = Status.BREAKDOWN
                 break
-            if not any_rr:
-                res.status = Status.STAGNATED
-                _log(res, alpha, omega, None, rn, do_rr, x, i, record, fbound)
-                break
-            r, k, w, s, l, z = replace(x, g)     # forced replacement
-            res.n_replacements += 1
-            do_rr = True
+            o_ = sc(omega)
+            # replacement decision for this iteration (uses only quantities known now)
+            do_rr = False
+            if rr_period > 0 and i > 0 and i % rr_period == 0 and rn >= math.sqrt(eps) * rn0:
+                do_rr = True                                             # reading R7
+            if rr_theta > 0 and rn <= rr_theta * rn_last_rr:
+                do_rr = True                                             # reading R8
+            if rr_auto and i > 0 and (fr_hist[i - 1] <= tau * rn_hist[i - 1] and fr_hist[i] > tau * rn_hist[i]):
+                do_rr = True                                             # Eq. (criterion)
+            x_old = x
+            x = (x + alpha * g.astype(np.float64)) + omega * u.astype(np.float64)   # l.17
+            r_new = q - o_ * y                  # l.18
+            k_new = u - o_ * (m - a_ * nv)      # l.19
+            w_new = y - o_ * (t - a_ * v)       # l.20
             if observer is not None:
-                observer("replace", i, dict(x=x, r=r, k=k, w=w, g=g, s=s, l=l, z=z))
+                observer("iter", i, dict(x=x_old, x_new=x, r=r, k=k, w=w, g=g, s=s, l=l, z=z, q=q, u=u,
+                                         y=y, m=m, t=t, n=nv, v=v, r_new=r_new, k_new=k_new,
+                                         w_new=w_new, g_prev=g_prev, l_prev=l_prev, s_prev=s_prev,
+                                         z_prev=z_prev, n_prev=n_prev, v_prev=v_prev, alpha=alpha,
+                                         beta=beta, omega=omega, omega_prev=omega_prev, replaced=do_rr))
             if fbound is not None:
-                fbound.reset(x, k, g, s, l, z)
+                fbound.step(alpha, beta, omega, omega_prev, x_old, r, k, w, g, s, l, z, q, u, y, m, t, nv, v)
+            r, k, w = r_new, k_new, w_new
+            if do_rr:                           # Eq. (rr), after l.20 (reading R6)
+                r, k, w, s, l, z = replace(x, g)
+                res.n_replacements += 1
+                if observer is not None:
+                    observer("replace", i, dict(x=x, r=r, k=k, w=w, g=g, s=s, l=l, z=z))
+                if fbound is not None:
+                    fbound.reset(x, k, g, s, l, z)
+            # l.21-24: second global reduction, overlapped with m = M^{-1} w, t = A m
             rho_new, rw, rs, rz = _dot(rhat, r), _dot(rhat, w), _dot(rhat, s), _dot(rhat, z)
-            rn = math.sqrt(_dot(r, r))
-            m = M.apply(w)
-            t = AT @ m
-        if do_rr:
-            rn_last_rr = rn
-        rn_hist.append(rn)
-        if fbound is not None:
-            fr_hist.append(fbound.f)
-        if omega == 0.0 or rho == 0.0:
-            res.status = Status.BREAKDOWN
-            _log(res, alpha, omega, None, rn, do_rr, x, i, record, fbound)
+            rr = _dot(r, r)
+            m = M.apply(w)                      # l.22
+            t = AT @ m                          # l.23
+            res.iterations = i + 1
+            rn = math.sqrt(rr)
+            if rn <= tol * bnorm:               # reading R5
+                tr = _true_res(A64, b, x)
+                if tr <= tol * bnorm:
+                    res.status = Status.OK
+                    _log(res, alpha, omega, None, rn, do_rr, x, i, record, fbound)
+                    break
+                if not any_rr:
+                    res.status = Status.STAGNATED
+                    _log(res, alpha, omega, None, rn, do_rr, x, i, record, fbound)
+                    break
+                r, k, w, s, l, z = replace(x, g)     # forced replacement
+                res.n_replacements += 1
+                do_rr = True
+                if observer is not None:
+                    observer("replace", i, dict(x=x, r=r, k=k, w=w, g=g, s=s, l=l, z=z))
+                if fbound is not None:
+                    fbound.reset(x, k, g, s, l, z)
+                rho_new, rw, rs, rz = _dot(rhat, r), _dot(rhat, w), _dot(rhat, s), _dot(rhat, z)
+                rn = math.sqrt(_dot(r, r))
+                m = M.apply(w)
+                t = AT @ m
+            if do_rr:
+                rn_last_rr = rn
+            rn_hist.append(rn)
+            if fbound is not None:
+                fr_hist.append(fbound.f)
+            if omega == 0.0 or rho == 0.0:
+                _log(res, alpha, omega, None, rn, do_rr, x, i, record, fbound)
+                if n_restarts < max_restarts:
+                    n_restarts += 1
+                    it += 1
+                    restart = True
+                    break
+                res.status = Status.BREAKDOWN
+                break
+            beta_new = (alpha / omega) * (rho_new / rho)                        # l.25
+            den = (rw + beta_new * rs) - (beta_new * omega) * rz                # l.26
+            alpha_new = rho_new / den if den != 0.0 else math.inf
+            _log(res, alpha, omega, beta_new, rn, do_rr, x, i, record, fbound)
+            if not (math.isfinite(beta_new) and den != 0.0 and math.isfinite(alpha_new)):
+                if n_restarts < max_restarts:
+                    n_restarts += 1
+                    it += 1
+                    restart = True
+                    break
+                res.status = Status.BREAKDOWN
+                break
+            alpha, beta, omega_prev, rho = alpha_new, beta_new, omega, rho_new
+            it += 1
+        if not restart:
             break
-        beta_new = (alpha / omega) * (rho_new / rho)                        # l.25
-        den = (rw + beta_new * rs) - (beta_new * omega) * rz                # l.26
-        alpha_new = rho_new / den if den != 0.0 else math.inf
-        _log(res, alpha, omega, beta_new, rn, do_rr, x, i, record, fbound)
-        if not (math.isfinite(beta_new) and den != 0.0 and math.isfinite(alpha_new)):
-            res.status = Status.BREAKDOWN
-            break
-        alpha, beta, omega_prev, rho = alpha_new, beta_new, omega, rho_new
+    res.n_restarts = n_restarts
     res.x = x
     res.rel_res_recursive = rn / bnorm
     res.rel_res_true = _true_res(A64, b, x) / bnorm

@@ -14,7 +14,8 @@ import torch
 from . import _capi as capi
 from ._capi import Result, STATUS_NAMES  # noqa: F401
 
-__all__ = ["Solver", "BatchSolver", "PBCGError", "build", "STATUS_NAMES", "test_barrier_timeout"]
+__all__ = ["Solver", "BatchSolver", "PBCGError", "build", "STATUS_NAMES", "test_barrier_timeout",
+           "SparseSolve", "sparse_solve"]
 
 
 class PBCGError(RuntimeError):
@@ -62,7 +63,7 @@ class Solver:
                  dia: torch.Tensor = None, precond: str = "jacobi", degree: int = 0,
                  precision: str = "fp64", tol: float = 1e-10, max_it: int = 10000, rr_period: int = 0,
                  rr_theta: float = 0.0, timeout_ms: float = 2000.0, grid_blocks: int = 0,
-                 block_threads: int = 0, stream: Optional[torch.cuda.Stream] = None):
+                 block_threads: int = 0, max_restarts: int = 0, stream: Optional[torch.cuda.Stream] = None):
         lib = _lib()
         self.n = int(n)
         self.stream = stream
@@ -93,6 +94,7 @@ class Solver:
             m.nnz = int(col.numel())
             m.row_ptr, m.col, m.val = _ptr(row_ptr), _ptr(col), _ptr(val)
             self._keep += [row_ptr, col, val]
+        self.nnz = int(m.nnz) if dia is None else 0
         p = capi.Precond(_PREC[precond], int(degree))
         self.opt = capi.Options()
         _check(lib.pbicgstab_default_options(C.byref(self.opt)), "default_options")
@@ -104,6 +106,7 @@ class Solver:
         self.opt.timeout_ms = timeout_ms
         self.opt.grid_blocks = grid_blocks
         self.opt.block_threads = block_threads
+        self.opt.max_restarts = max_restarts
         self.ctx = C.c_void_p()
         _check(lib.pbicgstab_create(C.byref(self.ctx), C.byref(m), C.byref(p), C.byref(self.opt),
                                     _stream_handle(stream)), "pbicgstab_create")
@@ -155,6 +158,36 @@ class Solver:
             raise PBCGError(st, capi.last_error())
         return x_host, res
 
+    def solve_multi(self, B: torch.Tensor, X: Optional[torch.Tensor] = None):
+        """Columns of B (n x nrhs, float64, CUDA) solved independently; returns (X, [Result])."""
+        if not (B.is_cuda and B.dtype == torch.float64 and B.dim() == 2 and B.shape[0] == self.n):
+            raise ValueError("B must be a CUDA float64 tensor of shape (n, nrhs)")
+        nrhs = B.shape[1]
+        Bc = B.t().contiguous()                       # column-major storage: column c contiguous
+        Xc = torch.zeros_like(Bc) if X is None else X.t().contiguous()
+        res = (capi.Result * nrhs)()
+        st = _lib().pbicgstab_solve_multi(self.ctx, nrhs, _ptr(Bc), _ptr(Xc), res)
+        if st in (capi.PBCG_INVALID_ARG, capi.PBCG_CUDA_ERROR, capi.PBCG_OUT_OF_MEMORY, capi.PBCG_TIMEOUT):
+            raise PBCGError(st, capi.last_error())
+        return Xc.t(), list(res)
+
+    def transpose(self) -> "Solver":
+        """A context for A^T (``pbicgstab_create_transpose``), same preconditioner and options."""
+        t = Solver.__new__(Solver)
+        t.n, t.stream, t._keep, t.opt = self.n, self.stream, [], capi.Options.from_buffer_copy(self.opt)
+        t.ctx = C.c_void_p()
+        _check(_lib().pbicgstab_create_transpose(C.byref(t.ctx), self.ctx), "pbicgstab_create_transpose")
+        return t
+
+    def value_grad(self, Lam: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
+        """-sum_c Lam[row_e, c] X[col_e, c] over the stored CSR entries (``pbicgstab_csr_value_grad``)."""
+        nrhs = X.shape[1]
+        Lc = Lam.t().contiguous()
+        Xc = X.t().contiguous()
+        g = torch.empty(self.nnz, dtype=torch.float64, device=X.device)
+        _check(_lib().pbicgstab_csr_value_grad(self.ctx, nrhs, _ptr(Lc), _ptr(Xc), _ptr(g)), "value_grad")
+        return g
+
     def spmv(self, x: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
         y = torch.empty_like(x) if y is None else y
         _check(_lib().pbicgstab_spmv(self.ctx, _ptr(x), _ptr(y)), "pbicgstab_spmv")
@@ -187,7 +220,8 @@ class BatchSolver:
 
     def __init__(self, row_off, nnz_off, row_ptr, col, val, precond: str = "jacobi", precision: str = "mixed",
                  tol: float = 1e-8, max_it: int = 1000, rr_period: int = 0, rr_theta: float = 0.0,
-                 grid_blocks: int = 0, block_threads: int = 0, stream: Optional[torch.cuda.Stream] = None):
+                 grid_blocks: int = 0, block_threads: int = 0, max_restarts: int = 0,
+                 stream: Optional[torch.cuda.Stream] = None):
         import numpy as np
         lib = _lib()
         self.row_off = np.ascontiguousarray(row_off, dtype=np.int64)
@@ -210,6 +244,7 @@ class BatchSolver:
         self.opt.tol, self.opt.max_it = tol, max_it
         self.opt.rr_period, self.opt.rr_theta = rr_period, rr_theta
         self.opt.grid_blocks, self.opt.block_threads = grid_blocks, block_threads
+        self.opt.max_restarts = max_restarts
         self.ctx = C.c_void_p()
         _check(lib.pbicgstab_batch_create(C.byref(self.ctx), C.byref(bt), C.byref(self.opt), _stream_handle(stream)),
                "pbicgstab_batch_create")
@@ -242,6 +277,46 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+class SparseSolve(torch.autograd.Function):
+    """X = A^{-1} B with A given by CSR values (differentiable in ``values`` and ``B``).
+
+    forward:  p-BiCGStab on A for every column of B (``pbicgstab_solve_multi``).
+    backward: adjoint p-BiCGStab on A^T (``pbicgstab_create_transpose``) for the upstream
+              gradient G = dL/dX: Lam = A^{-T} G; dL/dB = Lam; dL/dvalues = -sum_c Lam[row] X[col]
+              (``pbicgstab_csr_value_grad``).
+    """
+
+    @staticmethod
+    def forward(ctx, values, B, row_ptr, col, opts):
+        n = B.shape[0]
+        s = Solver(n, row_ptr=row_ptr, col=col, val=values.detach(), **opts)
+        X, res = s.solve_multi(B.detach())
+        bad = [r.status for r in res if r.status != capi.PBCG_OK]
+        if bad:
+            raise PBCGError(bad[0], "forward solve did not converge")
+        ctx.solver = s
+        ctx.save_for_backward(X)
+        return X
+
+    @staticmethod
+    def backward(ctx, G):
+        (X,) = ctx.saved_tensors
+        s = ctx.solver
+        st = s.transpose()
+        Lam, res = st.solve_multi(G.contiguous())
+        bad = [r.status for r in res if r.status != capi.PBCG_OK]
+        if bad:
+            raise PBCGError(bad[0], "adjoint solve did not converge")
+        gvals = s.value_grad(Lam, X) if ctx.needs_input_grad[0] else None
+        st.close()
+        return gvals, (Lam if ctx.needs_input_grad[1] else None), None, None, None
+
+
+def sparse_solve(values, B, row_ptr, col, **opts):
+    """Differentiable solve X = A^{-1} B (A in CSR with the given values)."""
+    return SparseSolve.apply(values, B, row_ptr, col, opts)
 
 
 def test_barrier_timeout(timeout_ms: float = 200.0, extra_arrivals: int = 1) -> str:

@@ -35,18 +35,19 @@ class Options(C.Structure):
                 ("rr_period", C.c_int32), ("rr_auto", C.c_int32), ("rr_theta", C.c_double),
                 ("timeout_ms", C.c_double), ("record_iterates", C.c_int32), ("hist_len", C.c_int32),
                 ("hist_x", C.c_void_p), ("hist_scalars", C.c_void_p),
-                ("grid_blocks", C.c_int32), ("block_threads", C.c_int32)]
+                ("grid_blocks", C.c_int32), ("block_threads", C.c_int32),
+                ("max_restarts", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("n_replacements", C.c_int32),
-                ("reserved0", C.c_int32), ("rel_res_recursive", C.c_double), ("rel_res_true", C.c_double),
+                ("n_restarts", C.c_int32), ("rel_res_recursive", C.c_double), ("rel_res_true", C.c_double),
                 ("time_ms", C.c_double)]
 
     def as_dict(self):
         return dict(status=STATUS_NAMES.get(self.status, str(self.status)), iterations=self.iterations,
-                    n_replacements=self.n_replacements, rel_res_recursive=self.rel_res_recursive,
-                    rel_res_true=self.rel_res_true, time_ms=self.time_ms)
+                    n_replacements=self.n_replacements, n_restarts=self.n_restarts,
+                    rel_res_recursive=self.rel_res_recursive, rel_res_true=self.rel_res_true, time_ms=self.time_ms)
 
 
 class Batch(C.Structure):
@@ -76,6 +77,9 @@ PROTOTYPES = {
     "pbicgstab_test_barrier_timeout": (C.c_int, [C.c_double, C.c_int32, C.POINTER(C.c_int32)]),
     "pbicgstab_solve_noalloc": (C.c_int, [C.POINTER(Matrix), C.POINTER(Precond), C.POINTER(Options), C.c_void_p,
                                           C.c_void_p, C.POINTER(Result), C.c_void_p]),
+    "pbicgstab_solve_multi": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pbicgstab_create_transpose": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p]),
+    "pbicgstab_csr_value_grad": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pbicgstab_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Batch), C.POINTER(Options), C.c_void_p]),
     "pbicgstab_batch_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(BatchResult)]),
     "pbicgstab_batch_destroy": (C.c_int, [C.c_void_p]),

@@ -38,6 +38,7 @@ struct BatchDev {
   int max_it;
   int rr_period;
   double rr_theta;
+  int max_restarts;
 };
 
 template <typename V>
@@ -101,11 +102,13 @@ __global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchDev d) 
       p.rr_period = d.rr_period;
       p.rr_theta = d.rr_theta;
       p.timeout_ns = 0;
+      p.max_restarts = d.max_restarts;
     }
     __syncthreads();
     BlockTeam team;
-    team.row0 = 0;
-    team.row1 = n;
+    team.first = 0;
+    team.stride = blockDim.x;
+    team.end = n;
     team.smem = smem;
     team.scal = scal;
     solve_body(p, team);
@@ -264,6 +267,7 @@ static BatchDev make_dev(pbcg_batch_ctx* c, const double* b, double* x) {
   d.max_it = c->opt.max_it;
   d.rr_period = c->opt.rr_period;
   d.rr_theta = c->opt.rr_theta;
+  d.max_restarts = c->opt.max_restarts;
   return d;
 }
 
@@ -330,6 +334,7 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
     return set_error(PBCG_INVALID_ARG, "bad solver options");
   if (opt->block_threads != 0 && (opt->block_threads < 32 || opt->block_threads > kMaxThreads || opt->block_threads % 32))
     return set_error(PBCG_INVALID_ARG, "block_threads must be 0 or a multiple of 32 in [32, 1024]");
+  if (opt->max_restarts < 0 || opt->max_restarts > 1000) return set_error(PBCG_INVALID_ARG, "max_restarts must be in [0, 1000]");
   const int ns = B->n_sys;
   if (B->row_off[0] != 0 || B->nnz_off[0] != 0) return set_error(PBCG_INVALID_ARG, "offsets must start at 0");
   for (int k = 0; k < ns; ++k) {

@@ -10,7 +10,6 @@
 
 #include "../../include/pbicgstab.h"
 #include "capi_internal.h"
-#include "solver.cuh"
 
 using namespace pbcg;
 
@@ -55,7 +54,8 @@ int sm_count() {
 // flags: bit0 row_ptr not monotone / wrong ends, bit1 column out of range or not
 // increasing, bit2 non-finite value, bit3 missing or zero diagonal (when required)
 __global__ void validate_csr_kernel(int n, long long nnz, const int* row_ptr, const int* col,
-                                    const void* val, int f32, int need_diag, int* flags, double* diag) {
+                                    const void* val, int f32, int need_diag, int* flags, double* diag,
+                                    int* bandwidth) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int f = 0;
@@ -67,17 +67,19 @@ __global__ void validate_csr_kernel(int n, long long nnz, const int* row_ptr, co
     return;
   }
   double dg = 0.0;
-  int prev = -1;
+  int prev = -1, bw = 0;
   for (int e = e0; e < e1; ++e) {
     const int c = col[e];
     if (c < 0 || c >= n || c <= prev) f |= 2;
     prev = c;
+    bw = max(bw, abs(c - i));
     const double v = f32 ? (double)((const float*)val)[e] : ((const double*)val)[e];
     if (!isfinite(v)) f |= 4;
     if (c == i) dg = v;
   }
   if (need_diag && dg == 0.0) f |= 8;
   diag[i] = dg;
+  if (bw) atomicMax(bandwidth, bw);
   if (f) atomicOr(flags, f);
 }
 
@@ -151,7 +153,7 @@ __global__ void true_res_partial_kernel(MatView<double> A, const double* b, cons
     v[0] = fma(r, r, v[0]);
     v[1] = fma(b[i], b[i], v[1]);
   }
-  block_publish<2>(v, smem, part);
+  block_publish<2>(v, smem, part, blockIdx.x);
 }
 
 __global__ void true_res_final_kernel(const double* part, int nparts, double* out) {
@@ -191,90 +193,22 @@ __global__ void barrier_timeout_kernel(unsigned* counter, int* err, int extra, u
 // ----------------------------------------------------------------------------
 // context
 // ----------------------------------------------------------------------------
-struct DevState {
-  DevResult res;
-  unsigned bar;
-  int err;
-  double true_rel;
-  int flags;
-  int reserved;
-};
-
-struct pbcg_ctx {
-  int n = 0;
-  long long nnz = 0;
-  int fmt = 0;
-  int precision = 0;
-  int prec_kind = 0;
-  int degree = 0;
-  cudaStream_t stream = nullptr;
-  pbcg_options opt{};
-  // matrix (device, owned)
-  int* row_ptr = nullptr;
-  int* col = nullptr;
-  double* val64 = nullptr;   // FP64 values (CSR nnz, DIA ndiag*n)
-  void* valAt = nullptr;     // hot operator values in T
-  void* valAu = nullptr;     // A in T (mixed: FP32 copy; FP64: aliases val64)
-  double* diag64 = nullptr;
-  double* dinv64 = nullptr;
-  void* dinvT = nullptr;
-  int ndiag = 0;
-  int offsets[kMaxDiag] = {0};
-  int ndiag_t = 0;           // diagonals stored in valAt (DIA fold drops the main one)
-  int offsets_t[kMaxDiag] = {0};
-  int at_unit_diag = 0;
-  // vectors + reductions
-  void* vecs = nullptr;
-  int nvec = 15;
-  double* part = nullptr;
-  int max_blocks = 0;
-  DevState* dstate = nullptr;
-  DevState* hstate = nullptr;  // pinned
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
-
-static size_t elem_size(int precision) { return precision == PBCG_MIXED ? sizeof(float) : sizeof(double); }
-
-template <typename V>
-static MatView<V> make_view(const pbcg_ctx* c, const V* val, bool hot) {
-  MatView<V> m;
-  memset(&m, 0, sizeof m);
-  m.fmt = c->fmt;
-  m.n = c->n;
-  m.row_ptr = c->row_ptr;
-  m.col = c->col;
-  m.val = val;
-  if (c->fmt == PBCG_FMT_DIA) {
-    if (hot) {
-      m.ndiag = c->ndiag_t;
-      m.unit_diag = c->at_unit_diag;
-      for (int d = 0; d < c->ndiag_t; ++d) m.off[d] = c->offsets_t[d];
-    } else {
-      m.ndiag = c->ndiag;
-      for (int d = 0; d < c->ndiag; ++d) m.off[d] = c->offsets[d];
-    }
-  }
-  return m;
-}
-
-MatView<double> pbcg_view64(const pbcg_ctx* c) { return make_view<double>(c, c->val64, false); }
-cudaStream_t pbcg_stream(const pbcg_ctx* c) { return c->stream; }
-int pbcg_n(const pbcg_ctx* c) { return c->n; }
-
 static void free_ctx(pbcg_ctx* c) {
   if (!c) return;
   if (c->valAu && c->valAu != (void*)c->val64) cudaFree(c->valAu);
   void* ptrs[] = {c->row_ptr, c->col, c->val64, c->valAt, c->diag64, c->dinv64, c->dinvT,
-                  c->vecs, c->part, c->dstate};
+                  c->vecs, c->part, c->dstate, c->multi_vecs, c->multi_part, c->multi_state, c->multi_params};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->hstate) cudaFreeHost(c->hstate);
+  if (c->multi_hstate) cudaFreeHost(c->multi_hstate);
+  if (c->multi_hparams) cudaFreeHost(c->multi_hparams);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
 }
 
-static pbcg_status check_options(const pbcg_options* o, long long n) {
+pbcg_status check_options(const pbcg_options* o, long long n) {
   if (o->precision != PBCG_FP64 && o->precision != PBCG_MIXED)
     return set_error(PBCG_INVALID_ARG, "options.precision must be PBCG_FP64 or PBCG_MIXED");
   if (o->max_it < 0) return set_error(PBCG_INVALID_ARG, "options.max_it must be >= 0");
@@ -289,6 +223,7 @@ static pbcg_status check_options(const pbcg_options* o, long long n) {
   if (o->block_threads != 0 && (o->block_threads < 32 || o->block_threads > kMaxThreads || o->block_threads % 32))
     return set_error(PBCG_INVALID_ARG, "options.block_threads must be 0 or a multiple of 32 in [32, 1024]");
   if (o->grid_blocks < 0) return set_error(PBCG_INVALID_ARG, "options.grid_blocks must be >= 0");
+  if (o->max_restarts < 0 || o->max_restarts > 1000) return set_error(PBCG_INVALID_ARG, "options.max_restarts must be in [0, 1000]");
   (void)n;
   return PBCG_OK;
 }
@@ -300,7 +235,7 @@ static int kernel_threads(const pbcg_ctx* c) {
   return c->opt.block_threads ? c->opt.block_threads : 512;
 }
 
-static pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads) {
+pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads) {
   const int nt = kernel_threads(c);
   int per_sm = 0;
   const void* k = c->precision == PBCG_MIXED ? kernel_ptr<float>() : kernel_ptr<double>();
@@ -350,7 +285,9 @@ static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
     CK(cudaMemcpyAsync(c->row_ptr, A->row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, c->stream), "copy row_ptr");
     if (c->nnz)
       CK(cudaMemcpyAsync(c->col, A->col, sizeof(int) * c->nnz, cudaMemcpyDeviceToDevice, c->stream), "copy col");
-    validate_csr_kernel<<<nb, 256, 0, c->stream>>>(n, c->nnz, c->row_ptr, c->col, A->val, f32, need_diag, dflags, c->diag64);
+    CK(cudaMemsetAsync(&c->dstate->reserved, 0, sizeof(int), c->stream), "memset");
+    validate_csr_kernel<<<nb, 256, 0, c->stream>>>(n, c->nnz, c->row_ptr, c->col, A->val, f32, need_diag, dflags, c->diag64,
+                                                    &c->dstate->reserved);
     CK(cudaGetLastError(), "validate kernel launch");
   } else {
     nval = (long long)c->ndiag * n;
@@ -364,9 +301,16 @@ static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
   const long long nbv = (nval + 255) / 256;
   if (nval) to_f64_kernel<<<(unsigned)nbv, 256, 0, c->stream>>>(nval, A->val, f32, c->val64);
   CK(cudaGetLastError(), "convert kernel");
-  int hflags = 0;
+  int hflags = 0, hbw = 0;
   CK(cudaMemcpyAsync(&hflags, dflags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy flags");
+  if (c->fmt == PBCG_FMT_CSR)
+    CK(cudaMemcpyAsync(&hbw, &c->dstate->reserved, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy bandwidth");
   CK(cudaStreamSynchronize(c->stream), "validate");
+  if (c->fmt == PBCG_FMT_CSR) {
+    c->bandwidth = hbw;
+  } else {
+    for (int d = 0; d < c->ndiag; ++d) c->bandwidth = std::max(c->bandwidth, std::abs(c->offsets[d]));
+  }
   if (hflags & 1) return set_error(PBCG_INVALID_ARG, "CSR row_ptr is not monotone from 0 to nnz");
   if (hflags & 2) return set_error(PBCG_INVALID_ARG, "CSR column index out of range or not strictly increasing in a row");
   if (hflags & 4) return set_error(PBCG_INVALID_ARG, "matrix has a non-finite value");
@@ -493,45 +437,7 @@ extern "C" pbcg_status pbicgstab_destroy(pbcg_ctx* c) {
   return PBCG_OK;
 }
 
-template <typename T>
-static SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int grid) {
-  SolverParams<T> p;
-  memset(&p, 0, sizeof p);
-  const int n = c->n;
-  p.n = n;
-  p.chunk = (n + grid - 1) / grid;
-  const T* at = c->valAt ? (const T*)c->valAt : (const T*)c->valAu;
-  p.At = make_view<T>(c, at, c->valAt != nullptr);
-  if (!c->valAt && c->fmt == PBCG_FMT_DIA) p.At = make_view<T>(c, at, false);
-  p.Au = make_view<T>(c, (const T*)c->valAu, false);
-  p.A64 = make_view<double>(c, c->val64, false);
-  p.dinv = c->prec_kind == PBCG_PREC_NONE ? nullptr
-           : (std::is_same<T, float>::value ? (const T*)c->dinvT : (const T*)c->dinv64);
-  p.prec = c->prec_kind;
-  p.degree = c->degree;
-  p.b = b;
-  p.x = x;
-  T* v = (T*)c->vecs;
-  T** slots[] = {&p.r, &p.rh, &p.k, &p.w, &p.g, &p.s, &p.l, &p.z, &p.v, &p.t, &p.nb, &p.m, &p.nn, &p.tmpa, &p.tmpb};
-  for (int j = 0; j < 15; ++j) *slots[j] = v + (size_t)j * n;
-  p.part = c->part;
-  p.bar = &c->dstate->bar;
-  p.err = &c->dstate->err;
-  p.res = &c->dstate->res;
-  p.hist_x = c->opt.hist_x;
-  p.K = c->opt.record_iterates;
-  p.hist_s = c->opt.hist_scalars;
-  p.hist_len = c->opt.hist_len;
-  p.tol = c->opt.tol;
-  p.max_it = c->opt.max_it;
-  p.rr_period = c->opt.rr_period;
-  p.rr_theta = c->opt.rr_theta;
-  const double tms = c->opt.timeout_ms > 0 ? c->opt.timeout_ms : 2000.0;
-  p.timeout_ns = (unsigned long long)(tms * 1e6);
-  return p;
-}
-
-static pbcg_status enqueue_true_residual(pbcg_ctx* c, const double* b, const double* x, double* out_dev) {
+pbcg_status enqueue_true_residual(pbcg_ctx* c, const double* b, const double* x, double* out_dev) {
   const int sms = sm_count();
   const int nb = std::min(c->max_blocks, std::max(1, std::min(2 * sms, (c->n + 255) / 256)));
   true_res_partial_kernel<<<nb, 256, 0, c->stream>>>(pbcg_view64(c), b, x, c->part);
@@ -569,6 +475,7 @@ static pbcg_status collect(pbcg_ctx* c, pbcg_result* res) {
   res->status = h.err ? PBCG_TIMEOUT : h.res.status;
   res->iterations = h.res.iterations;
   res->n_replacements = h.res.nrep;
+  res->n_restarts = h.res.nrestart;
   res->rel_res_recursive = h.res.rn_rel;
   res->rel_res_true = h.true_rel;
   res->time_ms = ms;

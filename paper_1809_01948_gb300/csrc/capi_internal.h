@@ -4,10 +4,143 @@
 #include <algorithm>
 #include <type_traits>
 #include <cuda_runtime.h>
+#include <cstring>
 #include "../../include/pbicgstab.h"
+#include "solver.cuh"
 
 namespace pbcg {
 pbcg_status set_error(pbcg_status st, const char* fmt, ...);
 pbcg_status cuda_status(cudaError_t e, const char* what);
 int sm_count();
 }  // namespace pbcg
+
+using pbcg::MatView;
+using pbcg::SolverParams;
+using pbcg::DevResult;
+using pbcg::kMaxDiag;
+using pbcg::kMaxDots;
+using pbcg::kMaxThreads;
+
+struct DevState {
+  DevResult res;
+  unsigned bar;
+  int err;
+  double true_rel;
+  int flags;
+  int reserved;
+};
+
+struct pbcg_ctx {
+  int n = 0;
+  long long nnz = 0;
+  int fmt = 0;
+  int precision = 0;
+  int prec_kind = 0;
+  int degree = 0;
+  cudaStream_t stream = nullptr;
+  pbcg_options opt{};
+  // matrix (device, owned)
+  int* row_ptr = nullptr;
+  int* col = nullptr;
+  double* val64 = nullptr;   // FP64 values (CSR nnz, DIA ndiag*n)
+  void* valAt = nullptr;     // hot operator values in T
+  void* valAu = nullptr;     // A in T (mixed: FP32 copy; FP64: aliases val64)
+  double* diag64 = nullptr;
+  double* dinv64 = nullptr;
+  void* dinvT = nullptr;
+  int ndiag = 0;
+  int offsets[kMaxDiag] = {0};
+  int ndiag_t = 0;           // diagonals stored in valAt (DIA fold drops the main one)
+  int offsets_t[kMaxDiag] = {0};
+  int at_unit_diag = 0;
+  int bandwidth = 0;         // max |col - row| over the stored entries
+  // vectors + reductions
+  void* vecs = nullptr;
+  int nvec = 15;
+  double* part = nullptr;
+  int max_blocks = 0;
+  DevState* dstate = nullptr;
+  DevState* hstate = nullptr;  // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // multi-RHS workspace (grown on demand by pbicgstab_solve_multi)
+  int multi_cap = 0;           // right-hand sides the buffers below hold
+  void* multi_vecs = nullptr;  // multi_cap * 15 * n values of T
+  double* multi_part = nullptr;
+  DevState* multi_state = nullptr;
+  DevState* multi_hstate = nullptr;   // pinned
+  void* multi_params = nullptr;       // multi_cap SolverParams<T>
+  void* multi_hparams = nullptr;      // pinned staging copy
+};
+
+inline size_t elem_size(int precision) { return precision == PBCG_MIXED ? sizeof(float) : sizeof(double); }
+
+template <typename V>
+inline MatView<V> make_view(const pbcg_ctx* c, const V* val, bool hot) {
+  MatView<V> m;
+  memset(&m, 0, sizeof m);
+  m.fmt = c->fmt;
+  m.n = c->n;
+  m.row_ptr = c->row_ptr;
+  m.col = c->col;
+  m.val = val;
+  if (c->fmt == PBCG_FMT_DIA) {
+    if (hot) {
+      m.ndiag = c->ndiag_t;
+      m.unit_diag = c->at_unit_diag;
+      for (int d = 0; d < c->ndiag_t; ++d) m.off[d] = c->offsets_t[d];
+    } else {
+      m.ndiag = c->ndiag;
+      for (int d = 0; d < c->ndiag; ++d) m.off[d] = c->offsets[d];
+    }
+  }
+  return m;
+}
+
+inline MatView<double> pbcg_view64(const pbcg_ctx* c) { return make_view<double>(c, c->val64, false); }
+
+
+pbcg_status check_options(const pbcg_options* o, long long n);
+pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads);
+pbcg_status enqueue_true_residual(pbcg_ctx* c, const double* b, const double* x, double* out_dev);
+
+template <typename T>
+inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int grid) {
+  SolverParams<T> p;
+  memset(&p, 0, sizeof p);
+  const int n = c->n;
+  p.n = n;
+  p.chunk = (n + grid - 1) / grid;
+  const T* at = c->valAt ? (const T*)c->valAt : (const T*)c->valAu;
+  p.At = make_view<T>(c, at, c->valAt != nullptr);
+  if (!c->valAt && c->fmt == PBCG_FMT_DIA) p.At = make_view<T>(c, at, false);
+  p.Au = make_view<T>(c, (const T*)c->valAu, false);
+  p.A64 = make_view<double>(c, c->val64, false);
+  p.dinv = c->prec_kind == PBCG_PREC_NONE ? nullptr
+           : (std::is_same<T, float>::value ? (const T*)c->dinvT : (const T*)c->dinv64);
+  p.prec = c->prec_kind;
+  p.degree = c->degree;
+  p.b = b;
+  p.x = x;
+  T* v = (T*)c->vecs;
+  T** slots[] = {&p.r, &p.rh, &p.k, &p.w, &p.g, &p.s, &p.l, &p.z, &p.v, &p.t, &p.nb, &p.m, &p.nn, &p.tmpa, &p.tmpb};
+  for (int j = 0; j < 15; ++j) *slots[j] = v + (size_t)j * n;
+  p.part = c->part;
+  p.bar = &c->dstate->bar;
+  p.err = &c->dstate->err;
+  p.res = &c->dstate->res;
+  p.hist_x = c->opt.hist_x;
+  p.K = c->opt.record_iterates;
+  p.hist_s = c->opt.hist_scalars;
+  p.hist_len = c->opt.hist_len;
+  p.tol = c->opt.tol;
+  p.max_it = c->opt.max_it;
+  p.rr_period = c->opt.rr_period;
+  p.rr_theta = c->opt.rr_theta;
+  const double tms = c->opt.timeout_ms > 0 ? c->opt.timeout_ms : 2000.0;
+  p.timeout_ns = (unsigned long long)(tms * 1e6);
+  p.max_restarts = c->opt.max_restarts;
+  p.strided = c->bandwidth > p.chunk / 2 ? 1 : 0;
+  return p;
+}
+
+

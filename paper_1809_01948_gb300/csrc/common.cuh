@@ -71,19 +71,19 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier over a co-resident (cooperatively launched) grid.  The counter
-// is monotone within a launch: barrier number `epoch` (1, 2, ...) completes when it
-// reaches epoch * gridDim.x.  Thread 0 of each block arrives (release) and polls
+// Barrier over `nblk` co-resident blocks (a cooperatively launched grid, or one
+// team of blocks inside it).  The counter is monotone within a launch: barrier
+// number `epoch` (1, 2, ...) completes when it reaches epoch * nblk.  Thread 0 of each block arrives (release) and polls
 // (acquire); the poll gives up after timeout_ns and raises *err = kTimeout.
 // Returns false when the grid must stop (timeout here or elsewhere).
-__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned epoch, int* err,
+__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned epoch, unsigned nblk, int* err,
                                              unsigned long long timeout_ns) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int ok = 1;
     red_release_add(counter, 1u);
-    const unsigned target = epoch * gridDim.x;
+    const unsigned target = epoch * nblk;
     const unsigned long long t0 = global_ns();
     unsigned spins = 0;
     while (ld_acquire_u32(counter) < target) {
@@ -169,11 +169,11 @@ __device__ __forceinline__ void block_reduce(const double (&in)[ND], double* wor
   __syncthreads();
 }
 
-// Block totals of ND per-thread values written to part[blockIdx.x * kMaxDots + d].
+// Block totals of ND per-thread values written to part[bid * kMaxDots + d].
 template <int ND>
-__device__ __forceinline__ void block_publish(double (&v)[ND], double* smem, double* part) {
+__device__ __forceinline__ void block_publish(double (&v)[ND], double* smem, double* part, int bid) {
   block_reduce<ND>(v, smem, smem + 32 * 8);
-  if (threadIdx.x < ND) part[blockIdx.x * kMaxDots + threadIdx.x] = smem[32 * 8 + threadIdx.x];
+  if (threadIdx.x < ND) part[bid * kMaxDots + threadIdx.x] = smem[32 * 8 + threadIdx.x];
 }
 
 // Block-wide sum returning the totals to every thread (used outside the solver loop).
@@ -188,7 +188,7 @@ __device__ __forceinline__ void block_sum(double (&v)[ND], double* smem) {
 // After a grid barrier: warp 0 of every block sums all blocks' partials in one fixed
 // order, so every block obtains bit-identical totals (the GLRED result).
 template <int ND>
-__device__ __forceinline__ void grid_combine(const double* part, double (&out)[ND], double* smem) {
+__device__ __forceinline__ void grid_combine(const double* part, int nblk, double (&out)[ND], double* smem) {
   constexpr int P = Pad<ND>::value;
   const int lane = threadIdx.x & 31;
   double* res = smem + 32 * 8;
@@ -196,7 +196,7 @@ __device__ __forceinline__ void grid_combine(const double* part, double (&out)[N
     double v[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) v[j] = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
+    for (int b = lane; b < nblk; b += 32) {
 #pragma unroll
       for (int d = 0; d < ND; ++d) v[d] += __ldcg(part + b * kMaxDots + d);
     }

@@ -62,7 +62,7 @@ pbcg_status scratch_address(void** out) {
 }
 
 __global__ void na_validate_csr(int n, long long nnz, const int* row_ptr, const int* col, const double* val,
-                                int need_diag, int* flags, double* diag) {
+                                int need_diag, int* flags, double* diag, int* bandwidth) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int f = 0;
@@ -71,16 +71,18 @@ __global__ void na_validate_csr(int n, long long nnz, const int* row_ptr, const 
   if (i == n - 1 && (long long)e1 != nnz) f |= 1;
   if (e1 < e0 || e0 < 0 || (long long)e1 > nnz) { atomicOr(flags, f | 1); return; }
   double dg = 0.0;
-  int prev = -1;
+  int prev = -1, bw = 0;
   for (int e = e0; e < e1; ++e) {
     const int c = col[e];
     if (c < 0 || c >= n || c <= prev) f |= 2;
     prev = c;
+    bw = max(bw, abs(c - i));
     if (!isfinite(val[e])) f |= 4;
     if (c == i) dg = val[e];
   }
   if (need_diag && dg == 0.0) f |= 8;
   diag[i] = dg;
+  if (bw) atomicMax(bandwidth, bw);
   if (f) atomicOr(flags, f);
 }
 
@@ -151,6 +153,7 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
     return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_noalloc supports no preconditioner or Jacobi");
   if (opt->max_it < 0 || !(opt->tol >= 0.0) || opt->rr_period < 0 || opt->rr_auto != 0 ||
       !(opt->rr_theta >= 0.0 && opt->rr_theta < 1.0) || opt->record_iterates < 0 ||
+      opt->max_restarts < 0 || opt->max_restarts > 1000 ||
       (opt->record_iterates > 0 && !opt->hist_x) || opt->hist_len < 0 || (opt->hist_len > 0 && !opt->hist_scalars))
     return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_noalloc: invalid options");
   const int n = (int)A->n;
@@ -198,7 +201,8 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   NCK(cudaMemsetAsync(state, 0, sizeof(NoAllocState), s), "memset scratch state");
   const int nb = (n + 255) / 256;
   if (A64.fmt == 0)
-    na_validate_csr<<<nb, 256, 0, s>>>(n, A->nnz, A->row_ptr, A->col, A64.val, jac, &state->flags, diag);
+    na_validate_csr<<<nb, 256, 0, s>>>(n, A->nnz, A->row_ptr, A->col, A64.val, jac, &state->flags, diag,
+                                        &state->reserved);
   else
     na_validate_dia<<<nb, 256, 0, s>>>(A64, jac, &state->flags, diag);
   NCK(cudaGetLastError(), "validation launch");
@@ -262,6 +266,12 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   p.rr_theta = opt->rr_theta;
   const double tms = opt->timeout_ms > 0 ? opt->timeout_ms : 2000.0;
   p.timeout_ns = (unsigned long long)(tms * 1e6);
+  p.max_restarts = opt->max_restarts;
+  // row order: the same rule as the context-based solver
+  int bandwidth = 0;
+  if (A64.fmt == 0) bandwidth = h.reserved;
+  else for (int d = 0; d < A64.ndiag; ++d) bandwidth = std::max(bandwidth, std::abs(A64.off[d]));
+  p.strided = bandwidth > p.chunk / 2 ? 1 : 0;
   void* args[] = {&p};
   NCK(cudaLaunchCooperativeKernel((const void*)pbicgstab_kernel<double>, grid, nt, args, 0, s), "cooperative launch");
   na_true_res<<<1, 1024, 0, s>>>(A64, b, x, &state->true_rel);
@@ -272,6 +282,7 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   res->status = h.err ? PBCG_TIMEOUT : h.res.status;
   res->iterations = h.res.iterations;
   res->n_replacements = h.res.nrep;
+  res->n_restarts = h.res.nrestart;
   res->rel_res_recursive = h.res.rn_rel;
   res->rel_res_true = h.true_rel;
   res->time_ms = -1.0;

@@ -30,7 +30,7 @@ struct DevResult {
   int status;
   int iterations;
   int nrep;
-  int reserved;
+  int nrestart;
   double rn_rel;   // ||r_last|| / ||b||
   double bnorm;
   double rn0;
@@ -50,7 +50,7 @@ struct SolverParams {
   const double* b;
   double* x;
   T *r, *rh, *k, *w, *g, *s, *l, *z, *v, *t, *nb, *m, *nn, *tmpa, *tmpb;
-  double* part;         // grid team: 3 partial sets of gridDim.x * kMaxDots doubles
+  double* part;         // grid team: 3 partial sets of (team blocks) * kMaxDots doubles
   unsigned* bar;
   int* err;
   DevResult* res;
@@ -63,6 +63,8 @@ struct SolverParams {
   int rr_period;
   double rr_theta;
   unsigned long long timeout_ns;
+  int max_restarts;     // restarts from the current iterate allowed after a breakdown
+  int strided;          // grid team row order: 1 grid-stride, 0 one contiguous chunk per block
 };
 
 // ---------------------------------------------------------------------------
@@ -73,7 +75,14 @@ struct SolverParams {
 //               __syncthreads and the partials stay in shared memory.
 // Both give every thread of the team bit-identical reduction results.
 struct GridTeam {
-  int row0, row1;
+  // Rows of this block: first, first + stride, ... below end.  Either one contiguous
+  // chunk per block (neighbours within about a chunk are re-read from L1/L2 by the same
+  // block), or grid-stride order: the whole grid sweeps a window of gridDim*blockDim
+  // consecutive rows together, so neighbours farther away than a chunk (the +-plane
+  // couplings of a 3D stencil) are read from L2 while the window still holds them.
+  int first, stride, end;
+  int bid;        // this block's index within the team
+  int nblk;       // blocks in the team (the whole grid, or one sub-grid of a multi solve)
   unsigned epoch;
   unsigned* bar;
   int* err;
@@ -81,20 +90,20 @@ struct GridTeam {
   double* part;
   double* smem;   // >= 32*8 + kMaxDots doubles
   double* scal;   // >= 8 doubles of shared memory for scalar broadcasts
-  __device__ __forceinline__ bool sync() { return grid_barrier(bar, ++epoch, err, timeout_ns); }
+  __device__ __forceinline__ bool sync() { return grid_barrier(bar, ++epoch, (unsigned)nblk, err, timeout_ns); }
   template <int ND>
   __device__ __forceinline__ void publish(double (&v)[ND], int set) {
-    block_publish<ND>(v, smem, part + (size_t)set * gridDim.x * kMaxDots);
+    block_publish<ND>(v, smem, part + (size_t)set * nblk * kMaxDots, bid);
   }
   template <int ND>
   __device__ __forceinline__ void combine(int set, double (&out)[ND]) {
-    grid_combine<ND>(part + (size_t)set * gridDim.x * kMaxDots, out, smem);
+    grid_combine<ND>(part + (size_t)set * nblk * kMaxDots, nblk, out, smem);
   }
-  __device__ __forceinline__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+  __device__ __forceinline__ bool leader() const { return bid == 0 && threadIdx.x == 0; }
 };
 
 struct BlockTeam {
-  int row0, row1;
+  int first, stride, end;
   double* smem;   // >= 32*8 + 3*kMaxDots doubles
   double* scal;   // >= 8 doubles of shared memory for scalar broadcasts
   __device__ __forceinline__ bool sync() { __syncthreads(); return true; }
@@ -122,14 +131,14 @@ __device__ __forceinline__ T minv_local(const SolverParams<T, VR>& p, T v, int i
 template <typename T, typename VR, typename Team>
 __device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T* src0, T* dst0, const T* src1,
                               T* dst1) {
-  const int row0 = team.row0, row1 = team.row1;
+  const int row0 = team.first, rstride = team.stride, row1 = team.end;
   const int d = p.degree;
   const T* prev0 = nullptr;
   const T* prev1 = nullptr;
   for (int j = 1; j <= d; ++j) {
     T* out0 = ((d - j) % 2 == 0) ? dst0 : p.tmpa;
     T* out1 = ((d - j) % 2 == 0) ? dst1 : p.tmpb;
-    for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+    for (int i = row0 + threadIdx.x; i < row1; i += rstride) {
       const T di = __ldg(p.dinv + i);
       {
         const T sv = src0[i];
@@ -158,10 +167,10 @@ __device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T*
 // is computed (stopping-test verification).
 template <typename T, typename VR, typename Team>
 __device__ void replace_r1(const SolverParams<T, VR>& p, Team& team, bool write) {
-  const int row0 = team.row0, row1 = team.row1;
+  const int row0 = team.first, rstride = team.stride, row1 = team.end;
   DAcc a_tr;
   const bool neu = p.prec == 2;
-  for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+  for (int i = row0 + threadIdx.x; i < row1; i += rstride) {
     const double r64 = p.b[i] - row_dot<double>(p.A64, p.x, i);
     if (write) {
       const T ri = T(r64);
@@ -185,11 +194,11 @@ __device__ void replace_r1(const SolverParams<T, VR>& p, Team& team, bool write)
 template <typename T, typename VR, typename Team>
 __device__ bool replace_r2(const SolverParams<T, VR>& p, Team& team) {
   using Acc = typename AccOf<T>::type;
-  const int row0 = team.row0, row1 = team.row1;
+  const int row0 = team.first, rstride = team.stride, row1 = team.end;
   const bool neu = p.prec == 2;
   if (neu && !neumann_apply(p, team, p.r, p.k, p.s, p.l)) return false;
   Acc a_rr, a_rw, a_rs, a_rz, a_r2;
-  for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+  for (int i = row0 + threadIdx.x; i < row1; i += rstride) {
     const T wi = neu ? row_dot<T>(p.Au, p.k, i) : row_dot<T>(p.At, p.r, i);
     const T zi = neu ? row_dot<T>(p.Au, p.l, i) : row_dot<T>(p.At, p.s, i);
     p.w[i] = wi;
@@ -207,14 +216,18 @@ template <typename T, typename VR, typename Team>
 __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   using Acc = typename AccOf<T>::type;
   const int n = p.n;
-  const int row0 = team.row0, row1 = team.row1;
+  const int row0 = team.first, rstride = team.stride, row1 = team.end;
   const bool neu = p.prec == 2;
   const bool leader = team.leader();
   int nrep = 0;
+  int nrestart = 0;
+  int it = 0;                 // completed iterations, across restarts
+  bool first = true;
+  double rn0 = 0.0;
 
 #define PBCG_SYNC() \
   do { if (!team.sync()) return; } while (0)
-#define PBCG_ROWS for (int i = row0 + threadIdx.x; i < row1; i += blockDim.x)
+#define PBCG_ROWS for (int i = row0 + threadIdx.x; i < row1; i += rstride)
   // FP64 division and square root are multi-instruction sequences on the scarce FP64
   // pipe: thread 0 evaluates them and the block reads the results from shared memory.
   double* const sc = team.scal;
@@ -227,11 +240,15 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   do {                                                                                   \
     if (leader) {                                                                        \
       p.res->status = (st); p.res->iterations = (its); p.res->nrep = nrep;               \
-      p.res->rn_rel = (rnv) / bn;                                                        \
+      p.res->nrestart = nrestart; p.res->rn_rel = (rnv) / bn;                            \
     }                                                                                    \
     return;                                                                              \
   } while (0)
 
+  // A breakdown (a zero or non-finite omega, (r0, r_i), beta or alpha denominator) can,
+  // if the options allow it, restart the method from the current iterate: lines 2-3
+  // again with x as the initial guess and the new r as the shadow vector.
+  for (;;) {
   // ---------------- initialisation (Algorithm 2, lines 2-3)
   {
     Acc a_rr;
@@ -284,22 +301,28 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     tolb = sc[3];
     PBCG_BCAST_DONE
   }
-  if (leader) { p.res->bnorm = bn; p.res->rn0 = rn; p.res->true_rel = -1.0; }
-  if (bn == 0.0) {            // b = 0: x = 0
-    PBCG_ROWS { p.x[i] = 0.0; }
-    if (leader) { p.res->status = kOK; p.res->iterations = 0; p.res->nrep = 0; p.res->rn_rel = 0.0; }
-    return;
+  if (first) {
+    if (leader) { p.res->bnorm = bn; p.res->rn0 = rn; p.res->true_rel = -1.0; }
+    if (bn == 0.0) {            // b = 0: x = 0
+      PBCG_ROWS { p.x[i] = 0.0; }
+      if (leader) {
+        p.res->status = kOK; p.res->iterations = 0; p.res->nrep = 0; p.res->nrestart = 0; p.res->rn_rel = 0.0;
+      }
+      return;
+    }
+    rn0 = rn;
+    first = false;
   }
-  if (rn <= tolb) PBCG_FINISH(kOK, 0, rn);
-  if (rw0 == 0.0 || !isfinite(alpha)) PBCG_FINISH(kBreakdown, 0, rn);
+  if (rn <= tolb) PBCG_FINISH(kOK, it, rn);
+  if (rw0 == 0.0 || !isfinite(alpha)) PBCG_FINISH(kBreakdown, it, rn);
   double beta = 0.0, omega_prev = 0.0;
-  const double rn0 = rn;
   bool rep_last = false;
+  bool restart = false;
   const double sqrt_eps = 1.4901161193847656e-08;  // sqrt(2^-52)
   const double rr_cutoff = sqrt_eps * rn0;          // periodic replacements stop below this
   double rr_theta_thr = p.rr_theta * rn;            // relative trigger threshold
 
-  for (int it = 0; it < p.max_it; ++it) {
+  for (; it < p.max_it; ++it) {
     // ---------------- m_i = M^{-1} w_i (Neumann only; on the fly otherwise)
     if (neu && !neumann_apply(p, team, p.w, p.m, (const T*)nullptr, (T*)nullptr)) return;
     // ---------------- pass A: t_i = A m_i; lines 5-11; partials of line 12
@@ -339,7 +362,10 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       omega = sc[0];
       PBCG_BCAST_DONE
     }
-    if (!isfinite(omega)) PBCG_FINISH(kBreakdown, it, rn);
+    if (!isfinite(omega)) {
+      if (nrestart < p.max_restarts) { ++nrestart; ++it; restart = true; break; }
+      PBCG_FINISH(kBreakdown, it, rn);
+    }
     bool do_rr = false;
     if (p.rr_period > 0 && it > 0 && it % p.rr_period == 0 && rn >= rr_cutoff) do_rr = true;
     if (p.rr_theta > 0.0 && rn <= rr_theta_thr) do_rr = true;
@@ -439,18 +465,25 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     alpha_new = sc[2];
     if (do_rr) rr_theta_thr = sc[3];
     PBCG_BCAST_DONE
-    if (omega == 0.0 || rho == 0.0) PBCG_FINISH(kBreakdown, it + 1, rn);
+    if (omega == 0.0 || rho == 0.0) {
+      if (nrestart < p.max_restarts) { ++nrestart; ++it; restart = true; break; }
+      PBCG_FINISH(kBreakdown, it + 1, rn);
+    }
     if (leader && it < p.hist_len) {
       double* h = p.hist_s + (size_t)it * PBCG_HS;
       h[0] = alpha; h[1] = omega; h[2] = beta_new; h[3] = rn / bn; h[4] = do_rr ? 1.0 : 0.0;
     }
-    if (!(isfinite(beta_new) && den != 0.0 && isfinite(alpha_new))) PBCG_FINISH(kBreakdown, it + 1, rn);
+    if (!(isfinite(beta_new) && den != 0.0 && isfinite(alpha_new))) {
+      if (nrestart < p.max_restarts) { ++nrestart; ++it; restart = true; break; }
+      PBCG_FINISH(kBreakdown, it + 1, rn);
+    }
     alpha = alpha_new;
     beta = beta_new;
     omega_prev = omega;
     rho = rho_new;
   }
-  PBCG_FINISH(kNotConverged, p.max_it, rn);
+  if (!restart) PBCG_FINISH(kNotConverged, p.max_it, rn);
+  }  // restarts
 #undef PBCG_SYNC
 #undef PBCG_ROWS
 #undef PBCG_FINISH
@@ -465,8 +498,17 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
   __shared__ double smem[32 * 8 + 3 * kMaxDots];
   __shared__ double scal[8];
   GridTeam team;
-  team.row0 = (int)min((long long)p.n, (long long)blockIdx.x * p.chunk);
-  team.row1 = min(p.n, team.row0 + p.chunk);
+  team.bid = blockIdx.x;
+  team.nblk = gridDim.x;
+  if (p.strided) {
+    team.first = blockIdx.x * blockDim.x;
+    team.stride = gridDim.x * blockDim.x;
+    team.end = p.n;
+  } else {
+    team.first = (int)min((long long)p.n, (long long)blockIdx.x * p.chunk);
+    team.stride = blockDim.x;
+    team.end = min(p.n, team.first + p.chunk);
+  }
   team.epoch = 0;
   team.bar = p.bar;
   team.err = p.err;
@@ -475,6 +517,41 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
   team.smem = smem;
   team.scal = scal;
   solve_body(p, team);
+}
+
+// Several independent solves that share the grid: team t is blocks
+// [t*bpt, (t+1)*bpt) and runs the whole algorithm on params[t] (its own b, x,
+// work vectors, barrier counter, partials and result) with team-local barriers.
+// Used for many right-hand sides with one matrix (the matrix is read by every
+// team; at moderate sizes it stays in L2).
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) pbicgstab_multi_kernel(const SolverParams<T>* params, int bpt) {
+  __shared__ double smem[32 * 8 + 3 * kMaxDots];
+  __shared__ double scal[8];
+  __shared__ SolverParams<T> sp;
+  const int t = blockIdx.x / bpt;
+  if (threadIdx.x == 0) sp = params[t];
+  __syncthreads();
+  GridTeam team;
+  team.bid = blockIdx.x - t * bpt;
+  team.nblk = bpt;
+  if (sp.strided) {
+    team.first = team.bid * blockDim.x;
+    team.stride = bpt * blockDim.x;
+    team.end = sp.n;
+  } else {
+    team.first = (int)min((long long)sp.n, (long long)team.bid * sp.chunk);
+    team.stride = blockDim.x;
+    team.end = min(sp.n, team.first + sp.chunk);
+  }
+  team.epoch = 0;
+  team.bar = sp.bar;
+  team.err = sp.err;
+  team.timeout_ns = sp.timeout_ns;
+  team.part = sp.part;
+  team.smem = smem;
+  team.scal = scal;
+  solve_body(sp, team);
 }
 
 }  // namespace pbcg

@@ -77,3 +77,19 @@ def test_mixed_with_replacement_reaches_1e10():
     m = oracle.pbicgstab(A, p.b, precond="jacobi", tol=1e-10, maxit=3000, mixed=True, rr_theta=1e-3)
     assert m.status == oracle.Status.OK and m.rel_res_true <= 1e-10
     assert m.x.dtype == np.float64
+
+
+def test_restart_after_breakdown_keeps_attainable_accuracy():
+    """Not in the paper (its breakdown handling is silent): with max_restarts a breakdown
+    restarts lines 2-3 of Algorithm 2 from the current iterate.  On TP2 pushed to an
+    unreachable tolerance the plain iteration diverges after stagnating and breaks down;
+    with restarts the true residual stays at the attainable level."""
+    A, _ = tp.normalise(tp.tp2(200))
+    N = A.n
+    As = A.to_scipy()
+    b = As @ np.full(N, 1 / np.sqrt(N))
+    plain = oracle.pbicgstab(As, b, tol=1e-16, maxit=1000, rr_period=100)
+    rs = oracle.pbicgstab(As, b, tol=1e-16, maxit=1000, rr_period=100, max_restarts=3)
+    assert plain.status == oracle.Status.BREAKDOWN and plain.n_restarts == 0
+    assert rs.n_restarts >= 1 and rs.status == oracle.Status.NOT_CONVERGED
+    assert rs.rel_res_true <= 1e-10 < plain.rel_res_true
