@@ -49,6 +49,18 @@ def bytes_per_row_iteration(precision: str, fmt: str = "dia", ndiag: int = 5, nn
     return float(vec + mat)
 
 
+def bytes_per_row_iteration_neumann(precision: str, degree: int = 2, nnz_row: float = 7.0) -> float:
+    """Algorithmic bytes per row and iteration with a degree-d Neumann preconditioner on a
+    CSR matrix: m and n must be stored, each M^{-1} application adds d Jacobi sweeps, so
+    the iteration streams 30 + 8d vectors (x in FP64) and reads the matrix 2 + 2d times
+    (values + int32 columns + row pointer).  Degree 2: 46 streams + 6 matrix reads."""
+    es = 8 if precision == "fp64" else 4
+    streams = 30 + 8 * degree
+    vec = (streams - 2) * es + 2 * 8
+    mat = (2 + 2 * degree) * (nnz_row * (es + 4) + 4)
+    return float(vec + mat)
+
+
 def bytes_per_row_replacement(precision: str, ndiag: int = 5) -> float:
     """Eq. (rr) pass pair: R1 reads b, x, g, z + 2 FP64 operator reads, writes r k s l n;
     R2 reads r, s, r0 + 2 folded operator reads, writes w z."""
@@ -151,17 +163,23 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    prob = tp.config2(GRID)
-    off, data = tp.csr_to_dia(prob.A)
-    dia = torch.from_numpy(data).to(dev)
+    if args.workload == "c2":
+        prob = tp.config2(args.grid or GRID)
+        off, data = tp.csr_to_dia(prob.A)
+        mat = dict(offsets=off.tolist(), dia=torch.from_numpy(data).to(dev), precond="jacobi")
+        workload = "convdiff2d_%dx%d_dia5_jacobi_tol1e-10" % ((args.grid or GRID), (args.grid or GRID))
+    else:
+        prob = tp.config3(args.grid or 256)
+        mat = dict(row_ptr=torch.from_numpy(prob.A.row_ptr).to(dev), col=torch.from_numpy(prob.A.col).to(dev),
+                   val=torch.from_numpy(prob.A.val).to(dev), precond="neumann", degree=2)
+        workload = "convdiff3d_%d^3_csr7_neumann2_tol1e-10" % (args.grid or 256)
     b = torch.from_numpy(prob.b).to(dev)
     n = prob.A.n
     variants = {
         "fp64": dict(precision="fp64", rr_period=100, rr_theta=0.0),
         "mixed": dict(precision="mixed", rr_period=args.mixed_period, rr_theta=args.theta),
     }
-    solvers = {k: pb.Solver(n, offsets=off.tolist(), dia=dia, precond="jacobi", tol=1e-10,
-                            max_it=args.max_it, **v) for k, v in variants.items()}
+    solvers = {k: pb.Solver(n, tol=1e-10, max_it=args.max_it, **mat, **v) for k, v in variants.items()}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
@@ -227,8 +245,7 @@ def run_gpu(args):
 
     # roofline of the dominant kernel (the persistent solver), per launch
     prec = args.precision
-    workload = "convdiff2d_1024x1024_dia5_jacobi_tol1e-10"
-    bpr = bytes_per_row_iteration(prec)
+    bpr = bytes_per_row_iteration(prec) if args.workload == "c2" else bytes_per_row_iteration_neumann(prec)
     alg_bytes = n * (bpr * head["iterations"] + bytes_per_row_replacement(prec) * head["n_replacements"])
     kernel_s = head["kernel_ms"] * 1e-3
     peaks = {}
@@ -243,7 +260,7 @@ def run_gpu(args):
            "frac": round(alg_bytes / kernel_s / 1e9 / hbm_peak, 4),
            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
            "bytes_per_row_iteration": bpr}
-    if prec == "fp64":
+    if prec == "fp64" and args.workload == "c2":
         # FP64 pipe bound: GB300 runs FP64 at 1/58 of FP32; nominal 1.25 TFLOP/s (measured 1.197)
         flops = fp64_flops_per_row_iteration() * n * head["iterations"]
         ach = flops / kernel_s / 1e12
@@ -255,10 +272,12 @@ def run_gpu(args):
         roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm["frac"], "traffic": traffic, "peak_source": hbm["peak_source"],
                 "bytes_per_row_iteration": bpr,
-                "note": "working set is L2-resident across iterations (DRAM traffic ~7 B/row/it)"}
+                }
+        if args.workload == "c2":
+            roof["note"] = "working set is L2-resident across iterations (DRAM traffic ~7 B/row/it)"
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and args.workload == "c2":
         cpu = cpu_baseline(args, head["iterations"], sample_iters=args.cpu_iters)
 
     if rank == 0:
@@ -267,7 +286,8 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms_per_solve"], 4),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
-            "config": {"workload": "convdiff2d_1024x1024_dia5_jacobi_tol1e-10", "n": n, "format": "DIA 5 diagonals FP64",
+            "config": {"workload": workload, "n": n,
+                       "format": "DIA 5 diagonals FP64" if args.workload == "c2" else "CSR int32, 7 nnz/row, FP64 values",
                        "precision": prec, "replacement": variants[prec], "global_batch": 1 * world,
                        "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps (256 MB write)"},
             "iterations": head["iterations"], "n_replacements": head["n_replacements"],
@@ -366,6 +386,9 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", action="store_true", help="measure the headline variant only")
+    ap.add_argument("--grid", type=int, default=0, help="grid size per dimension (profiling of smaller cases)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: 2D convection-diffusion 1024^2 DIA (default); c3: 3D 256^3 CSR Neumann-2")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

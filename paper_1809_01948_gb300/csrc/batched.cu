@@ -55,7 +55,7 @@ __device__ __forceinline__ MatView<V> csr_view(int n, const int* rp, const int* 
 }
 
 template <typename T, typename VR>
-__global__ void __launch_bounds__(kMaxThreads) batched_kernel(const BatchDev d) {
+__global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev d) {
   __shared__ double smem[32 * 8 + 3 * kMaxDots];
   __shared__ double scal[8];
   __shared__ int s_sys;

@@ -494,7 +494,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
 
 // One cooperative grid solves one system; block b owns rows [b*chunk, (b+1)*chunk).
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverParams<T> p) {
+__global__ void __launch_bounds__(kMaxThreads, 1) pbicgstab_kernel(const SolverParams<T> p) {
   __shared__ double smem[32 * 8 + 3 * kMaxDots];
   __shared__ double scal[8];
   GridTeam team;
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kMaxThreads) pbicgstab_kernel(const SolverPara
 // Used for many right-hand sides with one matrix (the matrix is read by every
 // team; at moderate sizes it stays in L2).
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) pbicgstab_multi_kernel(const SolverParams<T>* params, int bpt) {
+__global__ void __launch_bounds__(kMaxThreads, 1) pbicgstab_multi_kernel(const SolverParams<T>* params, int bpt) {
   __shared__ double smem[32 * 8 + 3 * kMaxDots];
   __shared__ double scal[8];
   __shared__ SolverParams<T> sp;
