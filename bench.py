@@ -380,8 +380,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--theta", type=float, default=0.0, help="mixed variant: relative replacement trigger")
-    ap.add_argument("--mixed-period", type=int, default=20, help="mixed variant: replacement period")
+    ap.add_argument("--theta", type=float, default=3e-3, help="mixed variant: relative replacement trigger")
+    ap.add_argument("--mixed-period", type=int, default=0, help="mixed variant: replacement period")
     ap.add_argument("--max-it", type=int, default=20000)
     ap.add_argument("--cpu-iters", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true")
