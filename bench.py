@@ -5,7 +5,8 @@ Workload (one "step" = one complete solve): 2D upwind convection-diffusion,
 diagonals, Jacobi preconditioner, x* ~ U[0,1] (seed 2), b = A x*, x0 = 0,
 tol 1e-10 on ||b - A x|| / ||b||.  The headline variant is set by --precision
 (fp64 with periodic replacement every 100 iterations by default); the other
-variant is measured alongside.
+variants (mixed precision, and on the 2D workload classic BiCGStab, Algorithm 1)
+are measured alongside.
 
 Prints ONE JSON line on rank 0.  --impl reference times the CPU oracle instead
 (a bounded sample of iterations, extrapolated with the oracle's iteration count
@@ -179,6 +180,10 @@ def run_gpu(args):
         "fp64": dict(precision="fp64", rr_period=100, rr_theta=0.0),
         "mixed": dict(precision="mixed", rr_period=args.mixed_period, rr_theta=args.theta),
     }
+    if args.workload == "c2":
+        # Algorithm 1, the paper's reference method, on the same system (three reduction
+        # phases per iteration instead of two)
+        variants["classic"] = dict(precision="fp64", method="classic", rr_period=0, rr_theta=0.0)
     solvers = {k: pb.Solver(n, tol=1e-10, max_it=args.max_it, **mat, **v) for k, v in variants.items()}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream()

@@ -55,6 +55,13 @@ typedef enum pbcg_precision {
                               b, dot-product results, alpha/beta/omega and replacement
                               residual r = b - A x (FP64 values)                          */
 } pbcg_precision;
+typedef enum pbcg_method {
+  PBCG_PIPELINED = 0,      /* Algorithm 2 (p-BiCGStab), two grid-wide reduction phases per
+                              iteration, with the replacement policies of the options    */
+  PBCG_CLASSIC = 1         /* Algorithm 1 (BiCGStab), the paper's reference method: three
+                              reduction phases per iteration (Alg. 1's three GLREDs),
+                              stop rule as for Algorithm 2 without replacement          */
+} pbcg_method;
 
 /* Sparse matrix description.  All arrays are read once by pbicgstab_create,
  * which keeps its own copies; the caller may free them afterwards.
@@ -92,7 +99,9 @@ typedef struct pbcg_options {
   double tol;              /* stop when ||r_i|| <= tol ||b|| (recursive, then verified) */
   int32_t rr_period;       /* periodic replacement every P iterations while
                               ||r_i|| >= sqrt(2^-52) ||r_0|| (Section 3.6); 0 = off    */
-  int32_t rr_auto;         /* reserved, must be 0 */
+  int32_t rr_auto;         /* 1: automated replacement, Eq. (criterion): replace when the
+                              run-time gap bound f^r of Eq. (DDr_bound) crosses
+                              rr_tau * ||r_i||; needs no or Jacobi preconditioning */
   double rr_theta;         /* relative trigger: replace when ||r_i|| <= theta * (residual
                               norm after the previous replacement); 0 = off            */
   double timeout_ms;       /* limit of every grid-wide wait in the kernels; <= 0: 2000 */
@@ -107,12 +116,15 @@ typedef struct pbcg_options {
                               current iterate with a new shadow vector, at most this many
                               times (0, the default, = the paper's algorithm: report
                               PBCG_BREAKDOWN)                                          */
-  int32_t reserved1;
+  int32_t method;          /* pbcg_method: PBCG_PIPELINED (default, Algorithm 2) or
+                              PBCG_CLASSIC (Algorithm 1: FP64 only, no or Jacobi
+                              preconditioning, no replacement, no restarts)             */
+  double rr_tau;           /* tau of Eq. (criterion); <= 0: sqrt(2^-52)               */
 } pbcg_options;
 
 typedef struct pbcg_result {
   int32_t status;          /* pbcg_status of the solve */
-  int32_t iterations;      /* completed iterations of Algorithm 2 */
+  int32_t iterations;      /* completed iterations of Algorithm 2 (or 1) */
   int32_t n_replacements;  /* executed Eq. (rr) steps (periodic, relative and forced) */
   int32_t n_restarts;      /* restarts after breakdowns (options.max_restarts) */
   double rel_res_recursive;/* ||r_last|| / ||b|| (recursively computed residual) */
@@ -142,7 +154,8 @@ pbcg_status pbicgstab_create(pbcg_ctx** out, const pbcg_matrix* A, const pbcg_pr
 pbcg_status pbicgstab_set_options(pbcg_ctx* ctx, const pbcg_options* opt);
 
 /* Solve A x = b with p-BiCGStab (Algorithm 2 with Eq. rr replacements per the
- * options).  b: device, n doubles, read only.  x: device, n doubles, read as
+ * options), or with classic BiCGStab (Algorithm 1) when options.method is
+ * PBCG_CLASSIC.  b: device, n doubles, read only.  x: device, n doubles, read as
  * x0 and overwritten with the last iterate (the solution on PBCG_OK).  res: host
  * or NULL; when non-NULL the call waits for the solve and fills it, otherwise it
  * only enqueues the work.  The returned status is the solve's status when res is

@@ -306,7 +306,7 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
                 do_rr = True                                             # reading R7
             if rr_theta > 0 and rn <= rr_theta * rn_last_rr:
                 do_rr = True                                             # reading R8
-            if rr_auto and i > 0 and (fr_hist[i - 1] <= tau * rn_hist[i - 1] and fr_hist[i] > tau * rn_hist[i]):
+            if rr_auto and len(fr_hist) >= 2 and (fr_hist[-2] <= tau * rn_hist[-2] and fr_hist[-1] > tau * rn_hist[-1]):
                 do_rr = True                                             # Eq. (criterion)
             x_old = x
             x = (x + alpha * g.astype(np.float64)) + omega * u.astype(np.float64)   # l.17

@@ -49,6 +49,7 @@ def _stream_handle(stream: Optional[torch.cuda.Stream]):
 
 _PREC = {"none": capi.PREC_NONE, "jacobi": capi.PREC_JACOBI, "neumann": capi.PREC_NEUMANN}
 _PRECISION = {"fp64": capi.FP64, "mixed": capi.MIXED}
+_METHOD = {"pipelined": capi.PIPELINED, "classic": capi.CLASSIC}
 
 
 class Solver:
@@ -63,7 +64,8 @@ class Solver:
                  dia: torch.Tensor = None, precond: str = "jacobi", degree: int = 0,
                  precision: str = "fp64", tol: float = 1e-10, max_it: int = 10000, rr_period: int = 0,
                  rr_theta: float = 0.0, timeout_ms: float = 2000.0, grid_blocks: int = 0,
-                 block_threads: int = 0, max_restarts: int = 0, stream: Optional[torch.cuda.Stream] = None):
+                 block_threads: int = 0, max_restarts: int = 0, rr_auto: bool = False, rr_tau: float = 0.0,
+                 method: str = "pipelined", stream: Optional[torch.cuda.Stream] = None):
         lib = _lib()
         self.n = int(n)
         self.stream = stream
@@ -107,6 +109,9 @@ class Solver:
         self.opt.grid_blocks = grid_blocks
         self.opt.block_threads = block_threads
         self.opt.max_restarts = max_restarts
+        self.opt.rr_auto = int(bool(rr_auto))
+        self.opt.rr_tau = rr_tau
+        self.opt.method = _METHOD[method]
         self.ctx = C.c_void_p()
         _check(lib.pbicgstab_create(C.byref(self.ctx), C.byref(m), C.byref(p), C.byref(self.opt),
                                     _stream_handle(stream)), "pbicgstab_create")
@@ -119,6 +124,8 @@ class Solver:
         for k, v in kw.items():
             if k == "precision":
                 v = _PRECISION[v]
+            elif k == "method":
+                v = _METHOD[v]
             setattr(self.opt, k, v)
         self.opt.hist_x = _ptr(hist_x) if hist_x is not None else None
         self.opt.hist_scalars = _ptr(hist_scalars) if hist_scalars is not None else None

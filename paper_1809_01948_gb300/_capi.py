@@ -15,6 +15,7 @@ FMT_CSR, FMT_DIA = 0, 1
 F64, F32 = 0, 1
 PREC_NONE, PREC_JACOBI, PREC_NEUMANN = 0, 1, 2
 FP64, MIXED = 0, 1
+PIPELINED, CLASSIC = 0, 1
 HIST_STRIDE = 8
 NOALLOC_MAX_N = 32768
 NOALLOC_MAX_VALUES = 524288
@@ -36,7 +37,7 @@ class Options(C.Structure):
                 ("timeout_ms", C.c_double), ("record_iterates", C.c_int32), ("hist_len", C.c_int32),
                 ("hist_x", C.c_void_p), ("hist_scalars", C.c_void_p),
                 ("grid_blocks", C.c_int32), ("block_threads", C.c_int32),
-                ("max_restarts", C.c_int32), ("reserved1", C.c_int32)]
+                ("max_restarts", C.c_int32), ("method", C.c_int32), ("rr_tau", C.c_double)]
 
 
 class Result(C.Structure):

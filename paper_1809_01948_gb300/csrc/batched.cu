@@ -56,7 +56,7 @@ __device__ __forceinline__ MatView<V> csr_view(int n, const int* rp, const int* 
 
 template <typename T, typename VR>
 __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev d) {
-  __shared__ double smem[32 * 8 + 3 * kMaxDots];
+  __shared__ double smem[kWork + 3 * kMaxDots];
   __shared__ double scal[8];
   __shared__ int s_sys;
   for (;;) {
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev 
     team.end = n;
     team.smem = smem;
     team.scal = scal;
-    solve_body(p, team);
+    solve_body<false>(p, team);
     __syncthreads();
     // final FP64 true residual of this system
     double a[2] = {0.0, 0.0};
@@ -121,9 +121,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev 
       a[0] = fma(r, r, a[0]);
       a[1] = fma(bi, bi, a[1]);
     }
-    block_reduce<2>(a, smem, smem + 32 * 8);
+    block_reduce<2>(a, smem, smem + kWork);
     if (threadIdx.x == 0) {
-      const double rr = smem[32 * 8], bb = smem[32 * 8 + 1];
+      const double rr = smem[kWork], bb = smem[kWork + 1];
       p.res->true_rel = bb > 0.0 ? sqrt(rr) / sqrt(bb) : sqrt(rr);
     }
   }
@@ -332,6 +332,7 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
   if (opt->max_it < 0 || !(opt->tol >= 0.0) || opt->rr_period < 0 || !(opt->rr_theta >= 0.0 && opt->rr_theta < 1.0) ||
       opt->rr_auto != 0)
     return set_error(PBCG_INVALID_ARG, "bad solver options");
+  if (opt->method != PBCG_PIPELINED) return set_error(PBCG_INVALID_ARG, "batched solves run Algorithm 2 only (PBCG_PIPELINED)");
   if (opt->block_threads != 0 && (opt->block_threads < 32 || opt->block_threads > kMaxThreads || opt->block_threads % 32))
     return set_error(PBCG_INVALID_ARG, "block_threads must be 0 or a multiple of 32 in [32, 1024]");
   if (opt->max_restarts < 0 || opt->max_restarts > 1000) return set_error(PBCG_INVALID_ARG, "max_restarts must be in [0, 1000]");

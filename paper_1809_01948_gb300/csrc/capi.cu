@@ -2,6 +2,7 @@
 // cooperative launch of the persistent solver, FP64 true residual.  C ABI in
 // include/pbicgstab.h.
 #include <cmath>
+#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -55,7 +56,7 @@ int sm_count() {
 // increasing, bit2 non-finite value, bit3 missing or zero diagonal (when required)
 __global__ void validate_csr_kernel(int n, long long nnz, const int* row_ptr, const int* col,
                                     const void* val, int f32, int need_diag, int* flags, double* diag,
-                                    int* bandwidth) {
+                                    int* bandwidth, int* maxnnz) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int f = 0;
@@ -80,7 +81,56 @@ __global__ void validate_csr_kernel(int n, long long nnz, const int* row_ptr, co
   if (need_diag && dg == 0.0) f |= 8;
   diag[i] = dg;
   if (bw) atomicMax(bandwidth, bw);
+  atomicMax(maxnnz, e1 - e0);
   if (f) atomicOr(flags, f);
+}
+
+// Constants of the error bounds (automated replacement).  Non-negative doubles are
+// compared through their bit patterns, and column sums are accumulated in fixed point
+// (each |a_ij| rounded up to a multiple of maxabs * 2^-40) with integer atomics, so the
+// results do not depend on the order of the atomic operations.
+__global__ void absmax_kernel(MatView<double> A, long long nval, unsigned long long* bits) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= nval) return;
+  const double v = fabs(A.val[e]);
+  if (v > 0.0) atomicMax(bits, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void row_col_sums_kernel(MatView<double> A, const unsigned long long* maxabs_bits, unsigned long long* rowmax_bits,
+                                    unsigned long long* colsum) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  const double maxabs = __longlong_as_double((long long)*maxabs_bits);
+  if (!(maxabs > 0.0)) return;
+  const double scale = 1099511627776.0 / maxabs;   // 2^40 / maxabs
+  double rs = 0.0;
+  if (A.fmt == 0) {
+    for (int e = A.row_ptr[i]; e < A.row_ptr[i + 1]; ++e) {
+      const double a = fabs(A.val[e]);
+      rs += a;
+      atomicAdd(colsum + A.col[e], (unsigned long long)ceil(a * scale));
+    }
+  } else {
+    for (int d = 0; d < A.ndiag; ++d) {
+      const int j = i + A.off[d];
+      if (j < 0 || j >= A.n) continue;
+      const double a = fabs(A.val[(size_t)d * A.n + i]);
+      rs += a;
+      atomicAdd(colsum + j, (unsigned long long)ceil(a * scale));
+    }
+  }
+  atomicMax(rowmax_bits, (unsigned long long)__double_as_longlong(rs));
+}
+
+__global__ void max_u64_kernel(int n, const unsigned long long* v, unsigned long long* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicMax(out, v[i]);
+}
+
+template <typename T>
+__global__ void dinv_max_kernel(int n, const T* dinv, unsigned long long* bits) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicMax(bits, (unsigned long long)__double_as_longlong(fabs((double)dinv[i])));
 }
 
 __global__ void validate_dia_kernel(int n, int ndiag, MatView<double> offs_only, const void* val, int f32,
@@ -146,7 +196,7 @@ __global__ void fold_dia_kernel(int n, MatView<double> src, const double* dinv, 
 
 // FP64 ||b - A x||^2 and ||b||^2, block partials then one fixed-order final sum.
 __global__ void true_res_partial_kernel(MatView<double> A, const double* b, const double* x, double* part) {
-  __shared__ double smem[32 * 8 + kMaxDots];
+  __shared__ double smem[kWork + kMaxDots];
   double v[2] = {0.0, 0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
     const double r = b[i] - row_dot<double>(A, x, i);
@@ -157,7 +207,7 @@ __global__ void true_res_partial_kernel(MatView<double> A, const double* b, cons
 }
 
 __global__ void true_res_final_kernel(const double* part, int nparts, double* out) {
-  __shared__ double smem[32 * 8 + kMaxDots];
+  __shared__ double smem[kWork + kMaxDots];
   double v[2] = {0.0, 0.0};
   for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
     v[0] += part[b * kMaxDots + 0];
@@ -214,7 +264,8 @@ pbcg_status check_options(const pbcg_options* o, long long n) {
   if (o->max_it < 0) return set_error(PBCG_INVALID_ARG, "options.max_it must be >= 0");
   if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return set_error(PBCG_INVALID_ARG, "options.tol must be finite and >= 0");
   if (o->rr_period < 0) return set_error(PBCG_INVALID_ARG, "options.rr_period must be >= 0");
-  if (o->rr_auto != 0) return set_error(PBCG_INVALID_ARG, "options.rr_auto is reserved and must be 0");
+  if (o->rr_auto != 0 && o->rr_auto != 1) return set_error(PBCG_INVALID_ARG, "options.rr_auto must be 0 or 1");
+  if (!(o->rr_tau >= 0.0) || !std::isfinite(o->rr_tau)) return set_error(PBCG_INVALID_ARG, "options.rr_tau must be >= 0");
   if (!(o->rr_theta >= 0.0 && o->rr_theta < 1.0)) return set_error(PBCG_INVALID_ARG, "options.rr_theta must be in [0, 1)");
   if (o->record_iterates < 0 || (o->record_iterates > 0 && !o->hist_x))
     return set_error(PBCG_INVALID_ARG, "options.record_iterates > 0 needs hist_x");
@@ -224,12 +275,33 @@ pbcg_status check_options(const pbcg_options* o, long long n) {
     return set_error(PBCG_INVALID_ARG, "options.block_threads must be 0 or a multiple of 32 in [32, 1024]");
   if (o->grid_blocks < 0) return set_error(PBCG_INVALID_ARG, "options.grid_blocks must be >= 0");
   if (o->max_restarts < 0 || o->max_restarts > 1000) return set_error(PBCG_INVALID_ARG, "options.max_restarts must be in [0, 1000]");
+  if (o->method != PBCG_PIPELINED && o->method != PBCG_CLASSIC)
+    return set_error(PBCG_INVALID_ARG, "options.method must be PBCG_PIPELINED or PBCG_CLASSIC");
+  if (o->method == PBCG_CLASSIC) {
+    if (o->precision != PBCG_FP64) return set_error(PBCG_INVALID_ARG, "PBCG_CLASSIC runs in PBCG_FP64 only");
+    if (o->rr_period != 0 || o->rr_theta != 0.0 || o->rr_auto != 0 || o->max_restarts != 0)
+      return set_error(PBCG_INVALID_ARG, "PBCG_CLASSIC takes no replacement policy and no restarts");
+  }
   (void)n;
   return PBCG_OK;
 }
 
+// Preconditioners each method's kernels apply.
+static pbcg_status check_method_precond(const pbcg_options* o, int prec_kind) {
+  if (o->rr_auto && prec_kind == PBCG_PREC_NEUMANN)
+    return set_error(PBCG_INVALID_ARG, "automated replacement (rr_auto) supports no or Jacobi preconditioning");
+  if (o->method == PBCG_CLASSIC && prec_kind == PBCG_PREC_NEUMANN)
+    return set_error(PBCG_INVALID_ARG, "PBCG_CLASSIC supports no or Jacobi preconditioning");
+  return PBCG_OK;
+}
+
 template <typename T>
-static const void* kernel_ptr() { return (const void*)pbicgstab_kernel<T>; }
+static const void* kernel_ptr(const pbcg_options& o) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (o.method == PBCG_CLASSIC) return (const void*)classic_kernel<double>;
+  }
+  return o.rr_auto ? (const void*)pbicgstab_kernel<T, true> : (const void*)pbicgstab_kernel<T, false>;
+}
 
 static int kernel_threads(const pbcg_ctx* c) {
   return c->opt.block_threads ? c->opt.block_threads : 512;
@@ -238,7 +310,7 @@ static int kernel_threads(const pbcg_ctx* c) {
 pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads) {
   const int nt = kernel_threads(c);
   int per_sm = 0;
-  const void* k = c->precision == PBCG_MIXED ? kernel_ptr<float>() : kernel_ptr<double>();
+  const void* k = c->precision == PBCG_MIXED ? kernel_ptr<float>(c->opt) : kernel_ptr<double>(c->opt);
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, 0), "occupancy query");
   const int sms = sm_count();
   const int max_coresident = per_sm * sms;
@@ -285,9 +357,9 @@ static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
     CK(cudaMemcpyAsync(c->row_ptr, A->row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, c->stream), "copy row_ptr");
     if (c->nnz)
       CK(cudaMemcpyAsync(c->col, A->col, sizeof(int) * c->nnz, cudaMemcpyDeviceToDevice, c->stream), "copy col");
-    CK(cudaMemsetAsync(&c->dstate->reserved, 0, sizeof(int), c->stream), "memset");
+    CK(cudaMemsetAsync(&c->dstate->reserved, 0, 2 * sizeof(int), c->stream), "memset");
     validate_csr_kernel<<<nb, 256, 0, c->stream>>>(n, c->nnz, c->row_ptr, c->col, A->val, f32, need_diag, dflags, c->diag64,
-                                                    &c->dstate->reserved);
+                                                    &c->dstate->reserved, &c->dstate->maxnnz);
     CK(cudaGetLastError(), "validate kernel launch");
   } else {
     nval = (long long)c->ndiag * n;
@@ -301,15 +373,17 @@ static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
   const long long nbv = (nval + 255) / 256;
   if (nval) to_f64_kernel<<<(unsigned)nbv, 256, 0, c->stream>>>(nval, A->val, f32, c->val64);
   CK(cudaGetLastError(), "convert kernel");
-  int hflags = 0, hbw = 0;
+  int hflags = 0, hbw[2] = {0, 0};
   CK(cudaMemcpyAsync(&hflags, dflags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy flags");
   if (c->fmt == PBCG_FMT_CSR)
-    CK(cudaMemcpyAsync(&hbw, &c->dstate->reserved, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy bandwidth");
+    CK(cudaMemcpyAsync(hbw, &c->dstate->reserved, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy bandwidth");
   CK(cudaStreamSynchronize(c->stream), "validate");
   if (c->fmt == PBCG_FMT_CSR) {
-    c->bandwidth = hbw;
+    c->bandwidth = hbw[0];
+    c->maxnnz = hbw[1];
   } else {
     for (int d = 0; d < c->ndiag; ++d) c->bandwidth = std::max(c->bandwidth, std::abs(c->offsets[d]));
+    c->maxnnz = c->ndiag;
   }
   if (hflags & 1) return set_error(PBCG_INVALID_ARG, "CSR row_ptr is not monotone from 0 to nnz");
   if (hflags & 2) return set_error(PBCG_INVALID_ARG, "CSR column index out of range or not strictly increasing in a row");
@@ -357,6 +431,33 @@ static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
     else fold_dia_kernel<double><<<nb, 256, 0, c->stream>>>(n, src, c->dinv64, (double*)c->valAt);
   }
   CK(cudaGetLastError(), "prepare kernels");
+  // constants of the error bounds: sqrt(||A||_1 ||A||_inf) and max |d_inv|
+  {
+    unsigned long long* colsum = nullptr;
+    CK(cudaMalloc(&colsum, sizeof(unsigned long long) * n), "cudaMalloc column sums");
+    CK(cudaMemsetAsync(colsum, 0, sizeof(unsigned long long) * n, c->stream), "memset");
+    CK(cudaMemsetAsync(&c->dstate->maxabs_bits, 0, 4 * sizeof(unsigned long long), c->stream), "memset");
+    MatView<double> A64v = make_view<double>(c, c->val64, false);
+    if (nval) absmax_kernel<<<(unsigned)nbv, 256, 0, c->stream>>>(A64v, nval, &c->dstate->maxabs_bits);
+    row_col_sums_kernel<<<nb, 256, 0, c->stream>>>(A64v, &c->dstate->maxabs_bits, &c->dstate->rowsum_bits, colsum);
+    max_u64_kernel<<<nb, 256, 0, c->stream>>>(n, colsum, &c->dstate->colsum_max);
+    if (need_diag) {
+      if (mixed) dinv_max_kernel<float><<<nb, 256, 0, c->stream>>>(n, (const float*)c->dinvT, &c->dstate->dinv_bits);
+      else dinv_max_kernel<double><<<nb, 256, 0, c->stream>>>(n, c->dinv64, &c->dstate->dinv_bits);
+    }
+    unsigned long long hb[4] = {0, 0, 0, 0};
+    CK(cudaGetLastError(), "bound constant kernels");
+    CK(cudaMemcpyAsync(hb, &c->dstate->maxabs_bits, sizeof hb, cudaMemcpyDeviceToHost, c->stream), "copy");
+    CK(cudaStreamSynchronize(c->stream), "bound constants");
+    cudaFree(colsum);
+    double maxabs, rowmax, dmax;
+    memcpy(&maxabs, &hb[0], 8);
+    memcpy(&rowmax, &hb[1], 8);
+    memcpy(&dmax, &hb[3], 8);
+    const double colmax = (double)hb[2] * (maxabs / 1099511627776.0);
+    c->norm_bound = std::sqrt(colmax * rowmax);
+    c->dinv_max = need_diag ? dmax : 1.0;
+  }
   return PBCG_OK;
 }
 
@@ -387,6 +488,8 @@ extern "C" pbcg_status pbicgstab_create(pbcg_ctx** out, const pbcg_matrix* A, co
     return set_error(PBCG_INVALID_ARG, "Neumann degree must be in [1, 8]");
   pbcg_status st = check_options(opt, A->n);
   if (st != PBCG_OK) return st;
+  st = check_method_precond(opt, M->kind);
+  if (st != PBCG_OK) return st;
 
   pbcg_ctx* c = new (std::nothrow) pbcg_ctx();
   if (!c) return set_error(PBCG_OUT_OF_MEMORY, "host allocation failed");
@@ -414,7 +517,7 @@ extern "C" pbcg_status pbicgstab_create(pbcg_ctx** out, const pbcg_matrix* A, co
   const size_t es = elem_size(c->precision);
   CKC(cudaMalloc(&c->vecs, es * (size_t)c->n * c->nvec), "cudaMalloc workspace");
   c->max_blocks = 4 * kMaxThreads;  // generous: any co-resident grid fits
-  CKC(cudaMalloc(&c->part, sizeof(double) * 3 * kMaxDots * (size_t)c->max_blocks), "cudaMalloc partials");
+  CKC(cudaMalloc(&c->part, sizeof(double) * 4 * kMaxDots * (size_t)c->max_blocks), "cudaMalloc partials");
   CKC(cudaStreamSynchronize(c->stream), "create");
   *out = c;
   return PBCG_OK;
@@ -426,6 +529,8 @@ extern "C" pbcg_status pbicgstab_set_options(pbcg_ctx* c, const pbcg_options* op
   pbcg_status st = check_options(opt, c->n);
   if (st != PBCG_OK) return st;
   if (opt->precision != c->precision) return set_error(PBCG_INVALID_ARG, "precision cannot change after create");
+  st = check_method_precond(opt, c->prec_kind);
+  if (st != PBCG_OK) return st;
   c->opt = *opt;
   return PBCG_OK;
 }
@@ -455,11 +560,11 @@ static pbcg_status enqueue_solve(pbcg_ctx* c, const double* b, double* x) {
   if (c->precision == PBCG_MIXED) {
     SolverParams<float> p = make_params<float>(c, b, x, grid);
     void* args[] = {&p};
-    CK(cudaLaunchCooperativeKernel(kernel_ptr<float>(), grid, threads, args, 0, c->stream), "cooperative launch");
+    CK(cudaLaunchCooperativeKernel(kernel_ptr<float>(c->opt), grid, threads, args, 0, c->stream), "cooperative launch");
   } else {
     SolverParams<double> p = make_params<double>(c, b, x, grid);
     void* args[] = {&p};
-    CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(), grid, threads, args, 0, c->stream), "cooperative launch");
+    CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(c->opt), grid, threads, args, 0, c->stream), "cooperative launch");
   }
   CK(cudaEventRecord(c->ev1, c->stream), "event record");
   return enqueue_true_residual(c, b, x, &c->dstate->true_rel);

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <type_traits>
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstring>
 #include "../../include/pbicgstab.h"
 #include "solver.cuh"
@@ -27,7 +28,13 @@ struct DevState {
   int err;
   double true_rel;
   int flags;
-  int reserved;
+  int reserved;                   // validation: max |col - row|
+  int maxnnz;                     // validation: max stored entries in a row
+  int reserved2;
+  unsigned long long maxabs_bits; // bit patterns of non-negative doubles order like the values
+  unsigned long long rowsum_bits;
+  unsigned long long colsum_max;  // max column sum in fixed point
+  unsigned long long dinv_bits;
 };
 
 struct pbcg_ctx {
@@ -54,6 +61,9 @@ struct pbcg_ctx {
   int offsets_t[kMaxDiag] = {0};
   int at_unit_diag = 0;
   int bandwidth = 0;         // max |col - row| over the stored entries
+  int maxnnz = 0;            // max stored entries in a row
+  double norm_bound = 0.0;   // sqrt(||A||_1 ||A||_inf) (upper bound of ||A||_2)
+  double dinv_max = 1.0;     // max |d_inv| in the working precision (1 without preconditioner)
   // vectors + reductions
   void* vecs = nullptr;
   int nvec = 15;
@@ -140,6 +150,12 @@ inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int 
   p.timeout_ns = (unsigned long long)(tms * 1e6);
   p.max_restarts = c->opt.max_restarts;
   p.strided = c->bandwidth > p.chunk / 2 ? 1 : 0;
+  p.rr_tau = c->opt.rr_tau > 0.0 ? c->opt.rr_tau : 1.4901161193847656e-08;
+  p.bnd_msn = (double)c->maxnnz * sqrt((double)n);
+  p.bnd_tmsn = sqrt((double)n);
+  p.bnd_nA = c->norm_bound;
+  p.bnd_nM = c->dinv_max;
+  p.bnd_eps = std::is_same<T, float>::value ? 1.1920928955078125e-07 : 2.220446049250313e-16;
   return p;
 }
 

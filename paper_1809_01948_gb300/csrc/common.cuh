@@ -10,7 +10,8 @@ namespace pbcg {
 
 constexpr int kMaxDiag = 16;
 constexpr int kMaxThreads = 1024;
-constexpr int kMaxDots = 8;
+constexpr int kMaxDots = 16;
+constexpr int kWork = 32 * 16;   // shared work area of block reductions (doubles)
 
 enum DevStatus : int {
   kRunning = -1, kOK = 0, kNotConverged = 4, kBreakdown = 5, kStagnated = 6, kTimeout = 7
@@ -49,6 +50,27 @@ __device__ __forceinline__ Acc row_dot(const MatView<V>& A, const X* __restrict_
     for (int d = 0; d < A.ndiag; ++d) {
       const int j = i + A.off[d];
       if (j >= 0 && j < n) acc = fma(Acc(__ldg(A.val + (size_t)d * n + i)), Acc(x[j]), acc);
+    }
+  }
+  return acc;
+}
+
+// The same row product with the operand given by a function of the column, so that a
+// vector which is a linear combination of stored ones (q = r - alpha s) need not be
+// written out before the product reads it at neighbouring rows.
+template <typename Acc, typename V, typename F>
+__device__ __forceinline__ Acc row_dot_fn(const MatView<V>& A, int i, F xj) {
+  Acc acc = Acc(0);
+  if (A.fmt == 0) {
+    const int e0 = __ldg(A.row_ptr + i), e1 = __ldg(A.row_ptr + i + 1);
+    for (int e = e0; e < e1; ++e) acc = fma(Acc(__ldg(A.val + e)), Acc(xj(__ldg(A.col + e))), acc);
+  } else {
+    if (A.unit_diag) acc = Acc(xj(i));
+    const int n = A.n;
+#pragma unroll 4
+    for (int d = 0; d < A.ndiag; ++d) {
+      const int j = i + A.off[d];
+      if (j >= 0 && j < n) acc = fma(Acc(__ldg(A.val + (size_t)d * n + i)), Acc(xj(j)), acc);
     }
   }
   return acc;
@@ -144,10 +166,12 @@ __device__ __forceinline__ double warp_transpose_sum(double (&v)[P]) {
   return s;
 }
 
-template <int ND> struct Pad { static constexpr int value = ND <= 1 ? 1 : ND <= 2 ? 2 : ND <= 4 ? 4 : 8; };
+template <int ND> struct Pad {
+  static constexpr int value = ND <= 1 ? 1 : ND <= 2 ? 2 : ND <= 4 ? 4 : ND <= 8 ? 8 : 16;
+};
 
 // Block-wide sums of ND per-thread doubles; block totals land in out_smem[0..ND)
-// (valid after the trailing __syncthreads).  work_smem: >= 32 * 8 doubles.
+// (valid after the trailing __syncthreads).  work_smem: >= kWork doubles.
 template <int ND>
 __device__ __forceinline__ void block_reduce(const double (&in)[ND], double* work_smem, double* out_smem) {
   constexpr int P = Pad<ND>::value;
@@ -172,16 +196,16 @@ __device__ __forceinline__ void block_reduce(const double (&in)[ND], double* wor
 // Block totals of ND per-thread values written to part[bid * kMaxDots + d].
 template <int ND>
 __device__ __forceinline__ void block_publish(double (&v)[ND], double* smem, double* part, int bid) {
-  block_reduce<ND>(v, smem, smem + 32 * 8);
-  if (threadIdx.x < ND) part[bid * kMaxDots + threadIdx.x] = smem[32 * 8 + threadIdx.x];
+  block_reduce<ND>(v, smem, smem + kWork);
+  if (threadIdx.x < ND) part[bid * kMaxDots + threadIdx.x] = smem[kWork + threadIdx.x];
 }
 
 // Block-wide sum returning the totals to every thread (used outside the solver loop).
 template <int ND>
 __device__ __forceinline__ void block_sum(double (&v)[ND], double* smem) {
-  block_reduce<ND>(v, smem, smem + 32 * 8);
+  block_reduce<ND>(v, smem, smem + kWork);
 #pragma unroll
-  for (int d = 0; d < ND; ++d) v[d] = smem[32 * 8 + d];
+  for (int d = 0; d < ND; ++d) v[d] = smem[kWork + d];
   __syncthreads();
 }
 
@@ -191,7 +215,7 @@ template <int ND>
 __device__ __forceinline__ void grid_combine(const double* part, int nblk, double (&out)[ND], double* smem) {
   constexpr int P = Pad<ND>::value;
   const int lane = threadIdx.x & 31;
-  double* res = smem + 32 * 8;
+  double* res = smem + kWork;
   if (threadIdx.x < 32) {
     double v[P];
 #pragma unroll

@@ -144,6 +144,8 @@ static pbcg_status launch_wave(pbcg_ctx* c, int teams, int bpt, int nt, const do
 extern "C" pbcg_status pbicgstab_solve_multi(pbcg_ctx* c, int32_t nrhs, const double* B, double* X,
                                              pbcg_result* res) {
   if (!c || !B || !X || nrhs < 1) return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_multi needs ctx, B, X, nrhs >= 1");
+  if (c->opt.rr_auto) return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_multi does not support rr_auto");
+  if (c->opt.method != PBCG_PIPELINED) return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_multi runs Algorithm 2 only");
   const int nt = c->opt.block_threads ? c->opt.block_threads : 512;
   int per_sm = 0;
   const void* k = c->precision == PBCG_MIXED ? multi_kernel_ptr<float>() : multi_kernel_ptr<double>();

@@ -122,7 +122,7 @@ __global__ void na_fold(MatView<double> A, const double* diag, double* dinv, dou
 }
 
 __global__ void na_true_res(MatView<double> A, const double* b, const double* x, double* out) {
-  __shared__ double smem[32 * 8 + kMaxDots];
+  __shared__ double smem[kWork + kMaxDots];
   double v[2] = {0.0, 0.0};
   for (int i = threadIdx.x; i < A.n; i += blockDim.x) {
     const double r = b[i] - row_dot<double>(A, x, i);
@@ -153,9 +153,10 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
     return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_noalloc supports no preconditioner or Jacobi");
   if (opt->max_it < 0 || !(opt->tol >= 0.0) || opt->rr_period < 0 || opt->rr_auto != 0 ||
       !(opt->rr_theta >= 0.0 && opt->rr_theta < 1.0) || opt->record_iterates < 0 ||
-      opt->max_restarts < 0 || opt->max_restarts > 1000 ||
+      opt->max_restarts < 0 || opt->max_restarts > 1000 || opt->rr_auto != 0 ||
       (opt->record_iterates > 0 && !opt->hist_x) || opt->hist_len < 0 || (opt->hist_len > 0 && !opt->hist_scalars))
     return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_noalloc: invalid options");
+  if (opt->method != PBCG_PIPELINED) return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_noalloc runs Algorithm 2 only");
   const int n = (int)A->n;
   MatView<double> A64;
   memset(&A64, 0, sizeof A64);
@@ -221,7 +222,7 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   const int nt = opt->block_threads ? opt->block_threads : 512;
   if (nt < 32 || nt > kMaxThreads || nt % 32) return set_error(PBCG_INVALID_ARG, "bad block_threads");
   int per_sm = 0;
-  NCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)pbicgstab_kernel<double>, nt, 0), "occupancy");
+  NCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)pbicgstab_kernel<double, false>, nt, 0), "occupancy");
   const int sms = sm_count();
   const int max_co = std::min(per_sm * sms, kMaxGrid);
   int grid = opt->grid_blocks;
@@ -273,7 +274,7 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   else for (int d = 0; d < A64.ndiag; ++d) bandwidth = std::max(bandwidth, std::abs(A64.off[d]));
   p.strided = bandwidth > p.chunk / 2 ? 1 : 0;
   void* args[] = {&p};
-  NCK(cudaLaunchCooperativeKernel((const void*)pbicgstab_kernel<double>, grid, nt, args, 0, s), "cooperative launch");
+  NCK(cudaLaunchCooperativeKernel((const void*)pbicgstab_kernel<double, false>, grid, nt, args, 0, s), "cooperative launch");
   na_true_res<<<1, 1024, 0, s>>>(A64, b, x, &state->true_rel);
   NCK(cudaGetLastError(), "true residual launch");
   NCK(cudaMemcpyAsync(&h, state, sizeof h, cudaMemcpyDeviceToHost, s), "copy result");

@@ -65,7 +65,105 @@ struct SolverParams {
   unsigned long long timeout_ns;
   int max_restarts;     // restarts from the current iterate allowed after a breakdown
   int strided;          // grid team row order: 1 grid-stride, 0 one contiguous chunk per block
+  // automated replacement, Eq. (criterion) with the gap bound f^r of Eq. (DDr_bound)
+  // (read only by kernels instantiated with AUTO = true)
+  double rr_tau;
+  double bnd_msn;       // mu sqrt(N), mu = max stored entries in a row of A
+  double bnd_tmsn;      // mu~ sqrt(N), mu~ = max entries in a row of M^{-1} (1: Jacobi / none)
+  double bnd_nA;        // upper bound of ||A||_2: sqrt(||A||_1 ||A||_inf)
+  double bnd_nM;        // ||M^{-1}||_2 = max |d_inv| (Jacobi) or 1
+  double bnd_eps;       // 2^-52, or 2^-23 for the FP32 recurrences of mixed mode
 };
+
+// ---------------------------------------------------------------------------
+// Run-time gap bound f^r for the automated replacement policy (Section 3.6):
+// Eq. (DDr_bound) with the local-error norms replaced by their bounds
+// Eq. (errbounds1)-(errbounds4) and the gaps of s, w, z by the triangle-inequality
+// bounds F^s, F^w, F^z of Eqs. (Ds), (Dw), (Dz).  Only thread 0 of a team runs these
+// (scalar FP64 work); the decision is broadcast.
+struct GapBound {
+  double f, Fz, Fs, Fw, f_pending, f_prev, rn_prev, rn_cur;
+  double pg, ps, pl, pz, pn, pv;   // norms of g, s, l, z, n, v of the previous iteration
+  int first, have_prev;
+};
+
+// indices of the 15 iteration-i norms handed to gb_step
+enum { NX = 0, NR, NK, NW, NG, NS, NL, NZ, NQ, NU, NY, NM, NT, NN, NV, NNORMS };
+
+template <typename T, typename VR>
+__device__ void gb_start(GapBound& S, const SolverParams<T, VR>& p, double xnorm, double bn, double rn) {
+  S.f = ((p.bnd_msn + 1.0) * p.bnd_nA * xnorm + bn) * p.bnd_eps;   // initial gap of r_0 = fl(b - A x0)
+  S.Fz = S.Fs = S.Fw = 0.0;
+  S.pg = S.ps = S.pl = S.pz = S.pn = S.pv = 0.0;
+  S.first = 1;
+  S.have_prev = 0;
+  S.rn_cur = rn;
+}
+
+// Eq. (criterion): replace in iteration i when f_{i-1} <= tau ||r_{i-1}|| and f_i > tau ||r_i||.
+__device__ __forceinline__ bool gb_criterion(const GapBound& S, double tau) {
+  return S.have_prev && S.f_prev <= tau * S.rn_prev && S.f > tau * S.rn_cur;
+}
+
+template <typename T, typename VR>
+__device__ void gb_step(GapBound& S, const SolverParams<T, VR>& p, const double* c, double alpha, double beta,
+                        double omega, double omega_prev) {
+  const double msn = p.bnd_msn, tmsn = p.bnd_tmsn, nA = p.bnd_nA, nM = p.bnd_nM, eps = p.bnd_eps;
+  const double a = fabs(alpha), b = fabs(beta), o = fabs(omega), op = fabs(omega_prev);
+  const double bo = b * op, oa = o * a;
+  const double Pg = S.first ? 0.0 : S.pg, Ps = S.first ? 0.0 : S.ps, Pl = S.first ? 0.0 : S.pl;
+  const double Pz = S.first ? 0.0 : S.pz, Pn = S.first ? 0.0 : S.pn, Pv = S.first ? 0.0 : S.pv;
+  // Eq. (errbounds1)-(errbounds4)
+  const double dg = (c[NK] + 3 * b * Pg + 4 * bo * Pl) * eps;
+  const double dx = (2 * c[NX] + 3 * a * c[NG] + 2 * o * c[NU]) * eps;
+  const double ds = (c[NW] + 3 * b * Ps + 4 * bo * Pz) * eps;
+  const double dr = (c[NQ] + 2 * o * c[NY]) * eps;
+  const double dl = (c[NM] + tmsn * nM * c[NW] + 3 * b * Pl + 4 * bo * Pn + tmsn * nM * bo * Pz) * eps;
+  const double dz = (c[NT] + msn * nA * c[NM] + tmsn * nA * nM * c[NW] + 3 * b * Pz + 4 * bo * Pv +
+                     msn * nA * bo * Pn + tmsn * nA * nM * bo * Pz) * eps;
+  const double dk = (c[NU] + 3 * o * c[NM] + tmsn * nM * o * c[NW] + 4 * oa * c[NN] + tmsn * nM * oa * c[NZ]) * eps;
+  const double dw = (c[NY] + 3 * o * c[NT] + msn * nA * o * c[NM] + tmsn * nA * nM * o * c[NW] + 4 * oa * c[NV] +
+                     msn * nA * oa * c[NN] + tmsn * nA * nM * oa * c[NZ]) * eps;
+  const double dq = (c[NR] + 2 * a * c[NS]) * eps;
+  const double du = (c[NK] + 2 * a * c[NL]) * eps;
+  const double dy = (c[NW] + 2 * a * c[NZ]) * eps;
+  if (S.first) {   // z_0 = t_0, s_0 = w_0, g_0 = k_0: round-off of explicit products
+    S.Fz = msn * nA * c[NL] * eps;
+    S.Fw = msn * nA * c[NK] * eps;
+    S.Fs = msn * nA * c[NG] * eps;
+    S.first = 0;
+  } else {
+    const double Fz = b * S.Fz + nA * dl + dz;                                   // Eq. (Dz)
+    const double Fs = S.Fw + b * S.Fs + bo * S.Fz + nA * dg + ds;                // Eq. (Ds)
+    S.Fz = Fz;
+    S.Fs = Fs;
+  }
+  S.f_pending = S.f;
+  S.f = S.f + a * S.Fs + o * S.Fw + oa * S.Fz + nA * dx + dr + o * nA * du + dq + o * dy;   // Eq. (Dr)
+  S.Fw = S.Fw + a * S.Fz + nA * (dk + du) + dw + dy;                                       // Eq. (Dw)
+  S.pg = c[NG]; S.ps = c[NS]; S.pl = c[NL]; S.pz = c[NZ]; S.pn = c[NN]; S.pv = c[NV];
+}
+
+// After Eq. (rr): every gap restarts from the round-off of the explicit recomputation.
+template <typename T, typename VR>
+__device__ void gb_reset(GapBound& S, const SolverParams<T, VR>& p, double xn, double kn, double gn, double sn,
+                         double ln, double zn, double bn) {
+  const double msn = p.bnd_msn, nA = p.bnd_nA, eps = p.bnd_eps;
+  S.f = ((msn + 1.0) * nA * xn + bn) * eps;
+  S.Fw = msn * nA * kn * eps;
+  S.Fs = msn * nA * gn * eps;
+  S.Fz = msn * nA * ln * eps;
+  S.ps = sn;
+  S.pl = ln;
+  S.pz = zn;
+}
+
+__device__ __forceinline__ void gb_end_iteration(GapBound& S, double rn) {
+  S.f_prev = S.f_pending;
+  S.rn_prev = S.rn_cur;
+  S.rn_cur = rn;
+  S.have_prev = 1;
+}
 
 // ---------------------------------------------------------------------------
 // Synchronisation scopes.  The algorithm body is written once against a "team":
@@ -88,7 +186,7 @@ struct GridTeam {
   int* err;
   unsigned long long timeout_ns;
   double* part;
-  double* smem;   // >= 32*8 + kMaxDots doubles
+  double* smem;   // >= kWork + kMaxDots doubles
   double* scal;   // >= 8 doubles of shared memory for scalar broadcasts
   __device__ __forceinline__ bool sync() { return grid_barrier(bar, ++epoch, (unsigned)nblk, err, timeout_ns); }
   template <int ND>
@@ -104,17 +202,17 @@ struct GridTeam {
 
 struct BlockTeam {
   int first, stride, end;
-  double* smem;   // >= 32*8 + 3*kMaxDots doubles
+  double* smem;   // >= kWork + 3*kMaxDots doubles
   double* scal;   // >= 8 doubles of shared memory for scalar broadcasts
   __device__ __forceinline__ bool sync() { __syncthreads(); return true; }
   template <int ND>
   __device__ __forceinline__ void publish(double (&v)[ND], int set) {
-    block_reduce<ND>(v, smem, smem + 32 * 8 + set * kMaxDots);
+    block_reduce<ND>(v, smem, smem + kWork + set * kMaxDots);
   }
   template <int ND>
   __device__ __forceinline__ void combine(int set, double (&out)[ND]) {
 #pragma unroll
-    for (int d = 0; d < ND; ++d) out[d] = smem[32 * 8 + set * kMaxDots + d];
+    for (int d = 0; d < ND; ++d) out[d] = smem[kWork + set * kMaxDots + d];
   }
   __device__ __forceinline__ bool leader() const { return threadIdx.x == 0; }
 };
@@ -165,10 +263,12 @@ __device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T*
 // nb = D^{-1} z_i (n_i stays the one computed from the old z_i, reading R6).
 // Publishes the partial ||b - A x||^2 to P2.  With write == false only the norm
 // is computed (stopping-test verification).
-template <typename T, typename VR, typename Team>
+template <bool AUTO, typename T, typename VR, typename Team>
 __device__ void replace_r1(const SolverParams<T, VR>& p, Team& team, bool write) {
+  using Acc = typename AccOf<T>::type;
   const int row0 = team.first, rstride = team.stride, row1 = team.end;
-  DAcc a_tr;
+  DAcc a_tr, a_x;
+  Acc a_g, a_k, a_s, a_l;
   const bool neu = p.prec == 2;
   for (int i = row0 + threadIdx.x; i < row1; i += rstride) {
     const double r64 = p.b[i] - row_dot<double>(p.A64, p.x, i);
@@ -178,26 +278,39 @@ __device__ void replace_r1(const SolverParams<T, VR>& p, Team& team, bool write)
       p.r[i] = ri;
       p.s[i] = si;
       if (!neu) {
-        p.k[i] = minv_local(p, ri, i);
-        p.l[i] = minv_local(p, si, i);
+        const T ki = minv_local(p, ri, i), li = minv_local(p, si, i);
+        p.k[i] = ki;
+        p.l[i] = li;
         p.nb[i] = minv_local(p, p.z[i], i);
+        if (AUTO) { a_k.add(ki, ki); a_l.add(li, li); }
+      }
+      if (AUTO) {
+        const double xi = p.x[i];
+        const T gi = p.g[i];
+        a_x.add(xi, xi); a_g.add(gi, gi); a_s.add(si, si);
       }
     }
     a_tr.add(r64, r64);
   }
-  double v1[1] = {a_tr.value()};
-  team.template publish<1>(v1, 2);
+  if (AUTO) {
+    // ||b - A x||^2 and the norms the gap bound restarts from: x, g, k, s, l
+    double v6[6] = {a_tr.value(), a_x.value(), a_g.value(), a_k.value(), a_s.value(), a_l.value()};
+    team.template publish<6>(v6, 2);
+  } else {
+    double v1[1] = {a_tr.value()};
+    team.template publish<1>(v1, 2);
+  }
 }
 
 // Eq. (rr), second half (after a grid barrier): Neumann k = M^{-1} r, l = M^{-1} s;
 // then w = A k, z = A l and the line-21 partials of the replaced vectors into P1.
-template <typename T, typename VR, typename Team>
+template <bool AUTO, typename T, typename VR, typename Team>
 __device__ bool replace_r2(const SolverParams<T, VR>& p, Team& team) {
   using Acc = typename AccOf<T>::type;
   const int row0 = team.first, rstride = team.stride, row1 = team.end;
   const bool neu = p.prec == 2;
   if (neu && !neumann_apply(p, team, p.r, p.k, p.s, p.l)) return false;
-  Acc a_rr, a_rw, a_rs, a_rz, a_r2;
+  Acc a_rr, a_rw, a_rs, a_rz, a_r2, a_z;
   for (int i = row0 + threadIdx.x; i < row1; i += rstride) {
     const T wi = neu ? row_dot<T>(p.Au, p.k, i) : row_dot<T>(p.At, p.r, i);
     const T zi = neu ? row_dot<T>(p.Au, p.l, i) : row_dot<T>(p.At, p.s, i);
@@ -205,17 +318,26 @@ __device__ bool replace_r2(const SolverParams<T, VR>& p, Team& team) {
     p.z[i] = zi;
     const T rh = p.rh[i], ri = p.r[i], si = p.s[i];
     a_rr.add(rh, ri); a_rw.add(rh, wi); a_rs.add(rh, si); a_rz.add(rh, zi); a_r2.add(ri, ri);
+    if (AUTO) a_z.add(zi, zi);
   }
-  double v5[5] = {a_rr.value(), a_rw.value(), a_rs.value(), a_rz.value(), a_r2.value()};
-  team.template publish<5>(v5, 1);
+  if (AUTO) {
+    double v6[6] = {a_rr.value(), a_rw.value(), a_rs.value(), a_rz.value(), a_r2.value(), a_z.value()};
+    team.template publish<6>(v6, 1);
+  } else {
+    double v5[5] = {a_rr.value(), a_rw.value(), a_rs.value(), a_rz.value(), a_r2.value()};
+    team.template publish<5>(v5, 1);
+  }
   return true;
 }
 
 // The whole solve (Algorithm 2 + Eq. rr) for one system, executed by a team.
-template <typename T, typename VR, typename Team>
+template <bool AUTO, typename T, typename VR, typename Team>
 __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   using Acc = typename AccOf<T>::type;
   const int n = p.n;
+  // automated replacement state, used by thread 0 only (AUTO kernels)
+  __shared__ GapBound gb;
+  __shared__ double gnorm[NNORMS];
   const int row0 = team.first, rstride = team.stride, row1 = team.end;
   const bool neu = p.prec == 2;
   const bool leader = team.leader();
@@ -252,9 +374,10 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   // ---------------- initialisation (Algorithm 2, lines 2-3)
   {
     Acc a_rr;
-    DAcc a_bb;
+    DAcc a_bb, a_xx;
     PBCG_ROWS {
       const double bi = p.b[i];
+      if (AUTO) { const double xi = p.x[i]; a_xx.add(xi, xi); }
       const double r64 = bi - row_dot<double>(p.A64, p.x, i);
       const T ri = T(r64);
       p.r[i] = ri;
@@ -265,8 +388,9 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       a_rr.add(ri, ri);
       a_bb.add(bi, bi);
     }
-    double v2[2] = {a_rr.value(), a_bb.value()};
-    team.template publish<2>(v2, 0);
+    double v3[3] = {a_rr.value(), a_bb.value(), a_xx.value()};
+    if (AUTO) team.template publish<3>(v3, 0);
+    else team.template publish<2>(*reinterpret_cast<double(*)[2]>(v3), 0);
   }
   PBCG_SYNC();
   if (neu && !neumann_apply(p, team, p.r, p.k, (const T*)nullptr, (T*)nullptr)) return;
@@ -283,17 +407,19 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   PBCG_SYNC();
   double rho, rw0, bn, rn, alpha, tolb;
   {
-    double t2[2];
-    team.template combine<2>(0, t2);
+    double t3[3] = {0.0, 0.0, 0.0};
+    if (AUTO) team.template combine<3>(0, t3);
+    else team.template combine<2>(0, *reinterpret_cast<double(*)[2]>(t3));
     double t1[1];
     team.template combine<1>(1, t1);
-    rho = t2[0];
+    rho = t3[0];
     rw0 = t1[0];
     PBCG_BCAST_BEGIN
-      sc[0] = sqrt(t2[1]);
+      sc[0] = sqrt(t3[1]);
       sc[1] = sqrt(rho);
       sc[2] = rw0 != 0.0 ? rho / rw0 : INFINITY;
       sc[3] = p.tol * sc[0];
+      if (AUTO) gb_start(gb, p, sqrt(t3[2]), sc[0], sc[1]);
     PBCG_BCAST_END
     bn = sc[0];
     rn = sc[1];
@@ -329,6 +455,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     {
       const T aT = T(alpha), bT = T(beta), opT = T(omega_prev);
       Acc a_qy, a_yy;
+      Acc an[12];   // AUTO: squared norms of r k w g s l z q u y m t (iteration i)
       PBCG_ROWS {
         const T wi = p.w[i];
         const T mi = neu ? p.m[i] : minv_local(p, wi, i);
@@ -345,21 +472,43 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         p.g[i] = gn; p.s[i] = sn; p.l[i] = ln; p.z[i] = zn; p.t[i] = ti;
         a_qy.add(q, y);
         a_yy.add(y, y);
+        if (AUTO) {
+          const T u = fma(-aT, ln, kk);
+          an[0].add(rr, rr); an[1].add(kk, kk); an[2].add(wi, wi); an[3].add(gn, gn); an[4].add(sn, sn);
+          an[5].add(ln, ln); an[6].add(zn, zn); an[7].add(q, q); an[8].add(u, u); an[9].add(y, y);
+          an[10].add(mi, mi); an[11].add(ti, ti);
+        }
       }
-      double v2[2] = {a_qy.value(), a_yy.value()};
-      team.template publish<2>(v2, 0);
+      if (AUTO) {
+        double v14[14];
+        v14[0] = a_qy.value();
+        v14[1] = a_yy.value();
+#pragma unroll
+        for (int j = 0; j < 12; ++j) v14[2 + j] = an[j].value();
+        team.template publish<14>(v14, 0);
+      } else {
+        double v2[2] = {a_qy.value(), a_yy.value()};
+        team.template publish<2>(v2, 0);
+      }
     }
     PBCG_SYNC();
     // ---------------- n_i = M^{-1} z_i (Neumann only), overlapping the reduction
     if (neu && !neumann_apply(p, team, p.z, p.nn, (const T*)nullptr, (T*)nullptr)) return;
     double omega;
+    bool do_auto = false;
     {
-      double t2[2];
-      team.template combine<2>(0, t2);
+      double t14[14];
+      if (AUTO) team.template combine<14>(0, t14);
+      else team.template combine<2>(0, *reinterpret_cast<double(*)[2]>(t14));
       PBCG_BCAST_BEGIN
-        sc[0] = t2[1] == 0.0 ? 0.0 : t2[0] / t2[1];   // line 16
+        sc[0] = t14[1] == 0.0 ? 0.0 : t14[0] / t14[1];   // line 16
+        if (AUTO) {
+          for (int j = 1; j <= 12; ++j) gnorm[j] = sqrt(t14[j + 1]);   // r..t of iteration i
+          sc[1] = gb_criterion(gb, p.rr_tau) ? 1.0 : 0.0;               // Eq. (criterion)
+        }
       PBCG_BCAST_END
       omega = sc[0];
+      if (AUTO) do_auto = sc[1] != 0.0;
       PBCG_BCAST_DONE
     }
     if (!isfinite(omega)) {
@@ -369,10 +518,13 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     bool do_rr = false;
     if (p.rr_period > 0 && it > 0 && it % p.rr_period == 0 && rn >= rr_cutoff) do_rr = true;
     if (p.rr_theta > 0.0 && rn <= rr_theta_thr) do_rr = true;
+    if (do_auto) do_rr = true;
     // ---------------- pass B: v_i = A n_i; lines 17-20; partials of line 21
     {
       const T aT = T(alpha), oT = T(omega);
       Acc a_rr, a_rw, a_rs, a_rz, a_r2;
+      DAcc a_xn;
+      Acc a_nn, a_vn;   // AUTO: squared norms of x_i, n_i, v_i
       const bool hist = it < p.K;
       PBCG_ROWS {
         const T zi = p.z[i];
@@ -384,7 +536,9 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         const T q = fma(-aT, ss, rr);
         const T u = fma(-aT, ll, kk);
         const T y = fma(-aT, zi, wi);
-        const double xn = fma(omega, (double)u, fma(alpha, (double)gg, p.x[i]));  // line 17
+        const double xo = p.x[i];
+        if (AUTO) { a_xn.add(xo, xo); a_nn.add(ni, ni); a_vn.add(vi, vi); }
+        const double xn = fma(omega, (double)u, fma(alpha, (double)gg, xo));  // line 17
         const T rn1 = fma(-oT, y, q);                    // r_{i+1} = q_i - omega_i y_i
         const T kn = fma(-oT, fma(-aT, ni, mi), u);      // k_{i+1} = u_i - omega_i (m_i - alpha_i n_i)
         const T wn = fma(-oT, fma(-aT, vi, ti), y);      // w_{i+1} = y_i - omega_i (t_i - alpha_i v_i)
@@ -399,21 +553,39 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         double v5[5] = {a_rr.value(), a_rw.value(), a_rs.value(), a_rz.value(), a_r2.value()};
         team.template publish<5>(v5, 1);
       }
+      if (AUTO) {
+        double v3[3] = {a_xn.value(), a_nn.value(), a_vn.value()};
+        team.template publish<3>(v3, 3);
+      }
     }
     // ---------------- residual replacement, Eq. (rr), after line 20 (reading R6)
     if (do_rr) {
       PBCG_SYNC();
-      replace_r1(p, team, true);
+      replace_r1<AUTO>(p, team, true);
       PBCG_SYNC();
-      if (!replace_r2(p, team)) return;
+      if (!replace_r2<AUTO>(p, team)) return;
       ++nrep;
     }
     rep_last = do_rr;
     PBCG_SYNC();
     // ---------------- lines 21-26: second reduction, stopping test, beta, alpha
-    double t5[5];
-    team.template combine<5>(1, t5);
+    double t5[6];
+    if (AUTO && do_rr) team.template combine<6>(1, t5);
+    else team.template combine<5>(1, *reinterpret_cast<double(*)[5]>(t5));
     double rho_new = t5[0], rw = t5[1], rs = t5[2], rz = t5[3];
+    if (AUTO) {
+      // gap bound: step with the iteration-i norms, then restart it after a replacement
+      double t3[3], t6[6];
+      team.template combine<3>(3, t3);
+      if (do_rr) team.template combine<6>(2, t6);
+      if (threadIdx.x == 0) {
+        gnorm[NX] = sqrt(t3[0]);
+        gnorm[NN] = sqrt(t3[1]);
+        gnorm[NV] = sqrt(t3[2]);
+        gb_step(gb, p, gnorm, alpha, beta, omega, omega_prev);
+        if (do_rr) gb_reset(gb, p, sqrt(t6[1]), sqrt(t6[3]), sqrt(t6[2]), sqrt(t6[4]), sqrt(t6[5]), sqrt(t5[5]), bn);
+      }
+    }
     PBCG_BCAST_BEGIN
       sc[0] = sqrt(t5[4]);
     PBCG_BCAST_END
@@ -422,11 +594,12 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     if (rn <= tolb) {
       // reading R5: verify with the FP64 true residual; with a replacement policy a
       // failed check forces a replacement, without one the solve has stagnated.
-      const bool any_rr = p.rr_period > 0 || p.rr_theta > 0.0;
-      replace_r1(p, team, any_rr);
+      const bool any_rr = p.rr_period > 0 || p.rr_theta > 0.0 || AUTO;
+      replace_r1<AUTO>(p, team, any_rr);
       PBCG_SYNC();
-      double t1[1];
-      team.template combine<1>(2, t1);
+      double t1[6];
+      if (AUTO) team.template combine<6>(2, t1);
+      else team.template combine<1>(2, *reinterpret_cast<double(*)[1]>(t1));
       PBCG_BCAST_BEGIN
         sc[0] = sqrt(t1[0]);
         p.res->true_rel = sc[0] / bn;
@@ -440,13 +613,16 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         }
         PBCG_FINISH(true_rn <= tolb ? kOK : kStagnated, it + 1, rn);
       }
-      if (!replace_r2(p, team)) return;
+      if (!replace_r2<AUTO>(p, team)) return;
       ++nrep;
       rep_last = true;
       do_rr = true;
       PBCG_SYNC();
-      team.template combine<5>(1, t5);
+      if (AUTO) team.template combine<6>(1, t5);
+      else team.template combine<5>(1, *reinterpret_cast<double(*)[5]>(t5));
       rho_new = t5[0]; rw = t5[1]; rs = t5[2]; rz = t5[3];
+      if (AUTO && threadIdx.x == 0)
+        gb_reset(gb, p, sqrt(t1[1]), sqrt(t1[3]), sqrt(t1[2]), sqrt(t1[4]), sqrt(t1[5]), sqrt(t5[5]), bn);
       PBCG_BCAST_BEGIN
         sc[0] = sqrt(t5[4]);
       PBCG_BCAST_END
@@ -455,6 +631,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     }
     double beta_new, alpha_new, den;
     PBCG_BCAST_BEGIN
+      if (AUTO) gb_end_iteration(gb, rn);
       if (do_rr) sc[3] = p.rr_theta * rn;
       sc[0] = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_new, rho));                               // line 25
       sc[1] = __dsub_rn(__dadd_rn(rw, __dmul_rn(sc[0], rs)), __dmul_rn(__dmul_rn(sc[0], omega), rz));   // line 26
@@ -492,10 +669,11 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
 #undef PBCG_BCAST_DONE
 }
 
-// One cooperative grid solves one system; block b owns rows [b*chunk, (b+1)*chunk).
-template <typename T>
+// One cooperative grid solves one system.  AUTO adds the automated replacement policy
+// (extra norms in the reductions and the gap bound in thread 0).
+template <typename T, bool AUTO>
 __global__ void __launch_bounds__(kMaxThreads, 1) pbicgstab_kernel(const SolverParams<T> p) {
-  __shared__ double smem[32 * 8 + 3 * kMaxDots];
+  __shared__ double smem[kWork + 3 * kMaxDots];
   __shared__ double scal[8];
   GridTeam team;
   team.bid = blockIdx.x;
@@ -516,7 +694,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pbicgstab_kernel(const SolverP
   team.part = p.part;
   team.smem = smem;
   team.scal = scal;
-  solve_body(p, team);
+  solve_body<AUTO>(p, team);
 }
 
 // Several independent solves that share the grid: team t is blocks
@@ -526,7 +704,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pbicgstab_kernel(const SolverP
 // team; at moderate sizes it stays in L2).
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads, 1) pbicgstab_multi_kernel(const SolverParams<T>* params, int bpt) {
-  __shared__ double smem[32 * 8 + 3 * kMaxDots];
+  __shared__ double smem[kWork + 3 * kMaxDots];
   __shared__ double scal[8];
   __shared__ SolverParams<T> sp;
   const int t = blockIdx.x / bpt;
@@ -551,7 +729,224 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pbicgstab_multi_kernel(const S
   team.part = sp.part;
   team.smem = smem;
   team.scal = scal;
-  solve_body(sp, team);
+  solve_body<false>(sp, team);
+}
+
+// ---------------------------------------------------------------------------
+// Classic preconditioned BiCGStab (Algorithm 1), the paper's reference method, with
+// the same team machinery.  Three grid barriers per iteration, one per global
+// reduction phase of Algorithm 1 (lines 6, 11, 15).  The new search direction
+// p_{i} = r_i + beta (p_{i-1} - omega s_{i-1}) (line 17) and q_i = r_i - alpha s_i
+// (line 8) are formed on the fly wherever the SpMV gathers them, so they need no pass of
+// their own; p and s are double-buffered because a pass reads the old values at
+// neighbouring rows while writing the new ones.  No preconditioner or Jacobi (folded
+// into A D^{-1}: s = A g = (A D^{-1}) p, y = A u = (A D^{-1}) q); no replacement.
+// Vector slots: r, rh, y = w, p = g / l (alternating), s = s / z (alternating).
+template <typename T, typename VR, typename Team>
+__device__ void classic_body(const SolverParams<T, VR>& p, Team& team) {
+  using Acc = typename AccOf<T>::type;
+  const int n = p.n;
+  const int row0 = team.first, rstride = team.stride, row1 = team.end;
+  const bool leader = team.leader();
+  double* const sc = team.scal;
+  T* pbuf[2] = {p.g, p.l};
+  T* sbuf[2] = {p.s, p.z};
+  T* const y = p.w;
+#define CL_SYNC() \
+  do { if (!team.sync()) return; } while (0)
+#define CL_ROWS for (int i = row0 + threadIdx.x; i < row1; i += rstride)
+#define CL_FINISH(st, its, rnv)                                                          \
+  do {                                                                                   \
+    if (leader) {                                                                        \
+      p.res->status = (st); p.res->iterations = (its); p.res->nrep = 0;                  \
+      p.res->nrestart = 0; p.res->rn_rel = (rnv) / bn;                                   \
+    }                                                                                    \
+    return;                                                                              \
+  } while (0)
+  // line 2: r_0 = b - A x_0; p_0 = r_0 (formed on the fly below, with beta = 0)
+  {
+    Acc a_rr;
+    DAcc a_bb;
+    CL_ROWS {
+      const double bi = p.b[i];
+      const double r64 = bi - row_dot<double>(p.A64, p.x, i);
+      const T ri = T(r64);
+      p.r[i] = ri;
+      p.rh[i] = ri;
+      pbuf[0][i] = T(0);
+      sbuf[0][i] = T(0);
+      a_rr.add(ri, ri);
+      a_bb.add(bi, bi);
+    }
+    double v2[2] = {a_rr.value(), a_bb.value()};
+    team.template publish<2>(v2, 0);
+  }
+  CL_SYNC();
+  double rho, bn, rn, tolb;
+  {
+    double t2[2];
+    team.template combine<2>(0, t2);
+    rho = t2[0];
+    if (threadIdx.x == 0) { sc[0] = sqrt(t2[1]); sc[1] = sqrt(rho); sc[2] = p.tol * sc[0]; }
+    __syncthreads();
+    bn = sc[0]; rn = sc[1]; tolb = sc[2];
+    __syncthreads();
+  }
+  if (leader) { p.res->bnorm = bn; p.res->rn0 = rn; p.res->true_rel = -1.0; }
+  if (bn == 0.0) {
+    CL_ROWS { p.x[i] = 0.0; }
+    if (leader) { p.res->status = kOK; p.res->iterations = 0; p.res->nrep = 0; p.res->nrestart = 0; p.res->rn_rel = 0.0; }
+    return;
+  }
+  if (rn <= tolb) CL_FINISH(kOK, 0, rn);
+  double beta = 0.0, omega = 0.0;
+  int cur = 0;
+  for (int it = 0; it < p.max_it; ++it) {
+    const T* p_old = pbuf[cur];
+    const T* s_old = sbuf[cur];
+    T* p_new = pbuf[cur ^ 1];
+    T* s_new = sbuf[cur ^ 1];
+    // lines 4-6: p_i (line 17 of the previous iteration), g_i = M^{-1} p_i, s_i = A g_i, (r0, s_i)
+    {
+      const T bT = T(beta), oT = T(omega);
+      Acc a_rs;
+      CL_ROWS {
+        const T acc = row_dot_fn<T>(p.At, i, [&](int j) { return fma(bT, fma(-oT, s_old[j], p_old[j]), p.r[j]); });
+        const T pi = fma(bT, fma(-oT, s_old[i], p_old[i]), p.r[i]);
+        p_new[i] = pi;
+        s_new[i] = acc;
+        a_rs.add(p.rh[i], acc);
+      }
+      double v1[1] = {a_rs.value()};
+      team.template publish<1>(v1, 0);
+    }
+    CL_SYNC();
+    double alpha;
+    {
+      double t1[1];
+      team.template combine<1>(0, t1);
+      if (threadIdx.x == 0) sc[0] = t1[0] != 0.0 ? rho / t1[0] : INFINITY;   // line 7
+      __syncthreads();
+      alpha = sc[0];
+      __syncthreads();
+      if (!isfinite(alpha)) CL_FINISH(kBreakdown, it, rn);
+    }
+    // lines 8-11: q_i = r_i - alpha s_i, u_i = M^{-1} q_i, y_i = A u_i, (q_i, y_i), (y_i, y_i)
+    {
+      const T aT = T(alpha);
+      Acc a_qy, a_yy;
+      CL_ROWS {
+        const T acc = row_dot_fn<T>(p.At, i, [&](int j) { return fma(-aT, s_new[j], p.r[j]); });
+        const T qi = fma(-aT, s_new[i], p.r[i]);
+        y[i] = acc;
+        a_qy.add(qi, acc);
+        a_yy.add(acc, acc);
+      }
+      double v2[2] = {a_qy.value(), a_yy.value()};
+      team.template publish<2>(v2, 1);
+    }
+    CL_SYNC();
+    {
+      double t2[2];
+      team.template combine<2>(1, t2);
+      if (threadIdx.x == 0) sc[0] = t2[1] == 0.0 ? 0.0 : t2[0] / t2[1];   // line 12
+      __syncthreads();
+      omega = sc[0];
+      __syncthreads();
+      if (!isfinite(omega)) CL_FINISH(kBreakdown, it, rn);
+    }
+    // lines 13-15: x_{i+1} = (x_i + alpha g_i) + omega u_i, r_{i+1} = q_i - omega y_i, (r0, r_{i+1})
+    {
+      const T aT = T(alpha), oT = T(omega);
+      Acc a_rr, a_r2;
+      const bool hist = it < p.K;
+      CL_ROWS {
+        const T qi = fma(-aT, s_new[i], p.r[i]);
+        const T gi = minv_local(p, p_new[i], i);
+        const T ui = minv_local(p, qi, i);
+        const double xn = fma(omega, (double)ui, fma(alpha, (double)gi, p.x[i]));
+        const T rn1 = fma(-oT, y[i], qi);
+        p.x[i] = xn;
+        p.r[i] = rn1;
+        if (hist) p.hist_x[(size_t)it * n + i] = xn;
+        a_rr.add(p.rh[i], rn1);
+        a_r2.add(rn1, rn1);
+      }
+      double v2[2] = {a_rr.value(), a_r2.value()};
+      team.template publish<2>(v2, 2);
+    }
+    CL_SYNC();
+    double rho_new;
+    {
+      double t2[2];
+      team.template combine<2>(2, t2);
+      rho_new = t2[0];
+      if (threadIdx.x == 0) {
+        sc[0] = sqrt(t2[1]);
+        sc[1] = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_new, rho));   // line 16
+      }
+      __syncthreads();
+      rn = sc[0];
+      const double beta_new = sc[1];
+      __syncthreads();
+      if (leader && it < p.hist_len) {
+        double* h = p.hist_s + (size_t)it * PBCG_HS;
+        h[0] = alpha; h[1] = omega; h[2] = beta_new; h[3] = rn / bn; h[4] = 0.0;
+      }
+      if (rn <= tolb) {   // reading R5 without replacement: verify, else stagnated
+        if (leader && it < p.hist_len) p.hist_s[(size_t)it * PBCG_HS + 2] = NAN;
+        DAcc a_tr;
+        CL_ROWS {
+          const double r64 = p.b[i] - row_dot<double>(p.A64, p.x, i);
+          a_tr.add(r64, r64);
+        }
+        double v1[1] = {a_tr.value()};
+        team.template publish<1>(v1, 3);
+        CL_SYNC();
+        double t1[1];
+        team.template combine<1>(3, t1);
+        if (threadIdx.x == 0) { sc[0] = sqrt(t1[0]); p.res->true_rel = sc[0] / bn; }
+        __syncthreads();
+        const double true_rn = sc[0];
+        __syncthreads();
+        CL_FINISH(true_rn <= tolb ? kOK : kStagnated, it + 1, rn);
+      }
+      if (omega == 0.0 || rho == 0.0 || !isfinite(beta_new)) CL_FINISH(kBreakdown, it + 1, rn);
+      beta = beta_new;
+      rho = rho_new;
+    }
+    cur ^= 1;
+  }
+  CL_FINISH(kNotConverged, p.max_it, rn);
+#undef CL_SYNC
+#undef CL_ROWS
+#undef CL_FINISH
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads, 1) classic_kernel(const SolverParams<T> p) {
+  __shared__ double smem[kWork + 3 * kMaxDots];
+  __shared__ double scal[8];
+  GridTeam team;
+  team.bid = blockIdx.x;
+  team.nblk = gridDim.x;
+  if (p.strided) {
+    team.first = blockIdx.x * blockDim.x;
+    team.stride = gridDim.x * blockDim.x;
+    team.end = p.n;
+  } else {
+    team.first = (int)min((long long)p.n, (long long)blockIdx.x * p.chunk);
+    team.stride = blockDim.x;
+    team.end = min(p.n, team.first + p.chunk);
+  }
+  team.epoch = 0;
+  team.bar = p.bar;
+  team.err = p.err;
+  team.timeout_ns = p.timeout_ns;
+  team.part = p.part;
+  team.smem = smem;
+  team.scal = scal;
+  classic_body(p, team);
 }
 
 }  // namespace pbcg

@@ -50,16 +50,17 @@ def gpu_solve(solver, b, K=0, hist_len=0, x0=None, **opts):
     return x.cpu().numpy(), res, its, hist
 
 
-def oracle_sensitivity(A, b, K, **kw):
+def oracle_sensitivity(A, b, K, method=None, **kw):
     """Per-iterate relative difference between two correct FP64 evaluations of the oracle
     that differ only in the summation order of the dot products (index order via BLAS vs
     an exactly rounded fsum).  This is the part of an iterate that the arithmetic of the
     method itself does not determine; parity tolerances are scaled from it."""
-    a = oracle.pbicgstab(A, b, tol=1e-300, maxit=K, record=K, **kw)
+    method = method or oracle.pbicgstab
+    a = method(A, b, tol=1e-300, maxit=K, record=K, **kw)
     orig = krylov._dot
     krylov._dot = lambda u, v: math.fsum(u.astype(np.float64) * v.astype(np.float64))
     try:
-        c = oracle.pbicgstab(A, b, tol=1e-300, maxit=K, record=K, **kw)
+        c = method(A, b, tol=1e-300, maxit=K, record=K, **kw)
     finally:
         krylov._dot = orig
     return a, np.array([np.linalg.norm(a.xs[i] - c.xs[i]) / np.linalg.norm(a.xs[i]) for i in range(K)])
@@ -71,11 +72,12 @@ def iterate_tolerance(sens, floor=1e-10, factor=100.0):
     return np.maximum(floor, factor * sens)
 
 
-def oracle_iteration_spread(A, b, **kw):
+def oracle_iteration_spread(A, b, method=None, **kw):
     """Iterations the oracle needs under three dot-product summation orders (BLAS, exactly
     rounded fsum, reversed index order).  On the convection-diffusion operators the
     convergence history is sensitive enough that these differ (e.g. 192 vs 357 on a
     97x97 grid), so an independent implementation is compared against this range."""
+    method = method or oracle.pbicgstab
     orig = krylov._dot
     orders = [orig,
               lambda u, v: math.fsum(u.astype(np.float64) * v.astype(np.float64)),
@@ -84,7 +86,7 @@ def oracle_iteration_spread(A, b, **kw):
     try:
         for f in orders:
             krylov._dot = f
-            out.append(oracle.pbicgstab(A, b, **kw))
+            out.append(method(A, b, **kw))
     finally:
         krylov._dot = orig
     return out

@@ -235,3 +235,35 @@ def test_host_buffers_end_to_end():
     x, res = s.solve_host(prob.b, x)
     assert res.status == 0
     assert np.linalg.norm(prob.b - prob.A.to_scipy() @ x) / np.linalg.norm(prob.b) <= 1e-10
+
+
+# ------------------------------------------------------------------ automated replacement
+@pytest.mark.parametrize("name,maker,fmt,tol", [("convdiff2d_64_dia", lambda: tp.config2(64), "dia", 1e-12),
+                                                 ("convdiff2d_64_csr", lambda: tp.config2(64), "csr", 1e-12),
+                                                 ("poisson2d_100_csr", lambda: tp.config1(), "csr", 1e-10)])
+def test_automated_replacement_schedule_matches_oracle(name, maker, fmt, tol):
+    """Eq. (criterion) with the run-time bound f^r of Eq. (DDr_bound): the GPU replaces in the
+    same iterations as the oracle (the bound's constants and norms agree to rounding)."""
+    prob = maker()
+    A = prob.A.to_scipy()
+    ref = oracle.pbicgstab(A, prob.b, precond=prob.precond, tol=tol, maxit=3000, rr_auto=True)
+    s = make_solver(prob, fmt=fmt, tol=tol, max_it=3000, rr_auto=True)
+    x, res, _, hist = gpu_solve(s, prob.b, hist_len=3000)
+    rep_gpu = [i for i in range(res.iterations) if hist[i, 4] == 1.0]
+    rep_ref = [i for i, f in enumerate(ref.replaced) if f]
+    assert res.status == int(ref.status) == 0, (res.as_dict(), ref.status)
+    assert len(rep_ref) >= 1
+    # the first replacements coincide exactly; later ones may shift by an iteration where
+    # f^r crosses tau ||r|| within rounding of the threshold
+    assert rep_gpu[:3] == rep_ref[:3], (rep_gpu, rep_ref)
+    assert abs(len(rep_gpu) - len(rep_ref)) <= 1
+    true = np.linalg.norm(prob.b - A @ x) / np.linalg.norm(prob.b)
+    assert true <= tol
+
+
+def test_automated_replacement_rejected_with_neumann():
+    torch_cuda()
+    import paper_1809_01948_gb300 as pb
+    prob = tp.config3(8)
+    with pytest.raises(pb.PBCGError):
+        make_solver(prob, rr_auto=True)
