@@ -115,10 +115,13 @@ class PipelinedProbe:
       ``gap``    -- ||Delta^r_i||, ||Delta^s_i||, ||Delta^w_i||, ||Delta^z_i||,
       ``gap_r_next`` -- ||Delta^r_{i+1}||,
       ``ident``  -- relative residuals of Eqs. (Dr), (Ds), (Dw), (Dz),
-      ``replaced``.
+      ``replaced``;
+    with ``keep_vectors`` also the delta and gap vectors (``delta_vec``, ``gap_vec``,
+    ``gap_next_vec``) and the iteration's scalars alpha_i, beta_i, omega_i, omega_{i-1}.
     """
 
-    def __init__(self, A64, b, precond_kind: str, dinv, degree: int, M):
+    def __init__(self, A64, b, precond_kind: str, dinv, degree: int, M, keep_vectors: bool = False):
+        self.keep_vectors = keep_vectors
         self.ops = _ExactOps(A64, precond_kind, dinv, degree)
         self.b = np.asarray(b, dtype=np.float64).astype(LD)
         self.c = bound_constants(A64, M)
@@ -194,6 +197,11 @@ class PipelinedProbe:
         self.records.append(dict(i=i, delta={k_: _nrm(v_) for k_, v_ in delta.items()}, bound=bounds,
                                  gap=dict(r=_nrm(Dr), s=_nrm(Ds), w=_nrm(Dw), z=_nrm(Dz)),
                                  gap_r_next=_nrm(Dr_next), ident=ident, replaced=bool(d["replaced"])))
+        if self.keep_vectors:   # the vectors themselves, extended precision
+            self.records[-1].update(delta_vec=delta, gap_vec=dict(r=Dr, s=Ds, w=Dw, z=Dz),
+                                    gap_next_vec=dict(r=Dr_next, w=Dw_next),
+                                    scalars=dict(alpha=d["alpha"], beta=d["beta"], omega=d["omega"],
+                                                 omega_prev=d["omega_prev"]))
         self.Ds_prev, self.Dz_prev, self.Dw_cur = Ds, Dz, Dw_next
 
 
