@@ -303,6 +303,22 @@ pbcg_status pbicgstab_solve_batched(const pbcg_batch* batch, const pbcg_options*
 pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_precond* M, const pbcg_options* opt,
                                     const double* b, double* x, pbcg_result* res, void* stream);
 
+/* Error propagation diagnostics (Section 2.4): column max-norms of the nine products
+ * of Eq. (all_error_matrices), U, OU, BA, UEA, BAEA, BPA, UC, BAC, BD, formed from the
+ * propagation matrices of Eq. (all_matrices) for the scalars of `iters` iterations of
+ * Algorithm 2 (the curves the paper plots against the iteration index).
+ *
+ * hist: device, iters rows of `stride` doubles (stride >= 3); row i holds alpha_i at
+ *   [0], omega_i at [1] and beta_{i+1} at [2] -- exactly the rows a solve writes to
+ *   options.hist_scalars (stride PBCG_HIST_STRIDE).  May be NULL when iters == 0.
+ * norms: device, 9 * (iters + 1) doubles, written: product p (in the order above) at
+ *   norms[p * (iters + 1) + j] for column j = 0 .. iters.  Column j depends on rows
+ *   0 .. j-1 only.  A non-finite scalar makes the columns it reaches NaN or Inf.
+ * iters: 0 .. 65536 (the work is O(iters^2)).  stream: as elsewhere.  Enqueues only.
+ * Errors: INVALID_ARG (NULL pointer, stride < 3, iters out of range), CUDA_ERROR. */
+pbcg_status pbicgstab_propagation_norms(const double* hist, int32_t stride, int32_t iters, double* norms,
+                                        void* stream);
+
 /* Test hook for the fault-detection path: launches a cooperative grid whose
  * blocks wait at a barrier for `extra_arrivals` more blocks than exist, so the
  * wait can only end by its timeout.  Returns PBCG_OK when the kernel gave up

@@ -76,10 +76,7 @@ def propagation_matrices(alpha: Sequence[float], beta_next: Sequence[float],
     beta = np.concatenate([[np.nan], beta_next])     # beta[j] = beta_j, j >= 1
 
     def bprod(k, j):   # beta_{k+1} ... beta_j (empty product = 1)
-        out = 1.0
-        for l_ in range(k + 1, j + 1):
-            out *= beta[l_]
-        return out
+        return float(np.prod(beta[k + 1:j + 1]))
 
     Am, Bm, Em, Pm, Cm, Dm, Om, Um = (np.zeros((m, m)) for _ in range(8))
     for j in range(m):

@@ -326,6 +326,22 @@ def sparse_solve(values, B, row_ptr, col, **opts):
     return SparseSolve.apply(values, B, row_ptr, col, opts)
 
 
+def propagation_norms(hist: torch.Tensor, iters: int, stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """Column max-norms of the error propagation products (``pbicgstab_propagation_norms``).
+
+    ``hist``: CUDA float64 tensor holding at least ``iters`` rows of ``capi.HIST_STRIDE``
+    doubles, as a solve writes them to ``hist_scalars``.  Returns a (9, iters + 1) CUDA
+    tensor, rows in ``capi.PROPAGATION_PRODUCTS`` order."""
+    if not (hist.is_cuda and hist.dtype == torch.float64 and hist.is_contiguous()):
+        raise ValueError("hist must be a contiguous CUDA float64 tensor")
+    if hist.numel() < iters * capi.HIST_STRIDE:
+        raise ValueError("hist holds fewer than iters rows")
+    out = torch.empty(len(capi.PROPAGATION_PRODUCTS), iters + 1, dtype=torch.float64, device=hist.device)
+    _check(_lib().pbicgstab_propagation_norms(_ptr(hist), capi.HIST_STRIDE, int(iters), _ptr(out),
+                                              _stream_handle(stream)), "pbicgstab_propagation_norms")
+    return out
+
+
 def test_barrier_timeout(timeout_ms: float = 200.0, extra_arrivals: int = 1) -> str:
     st = C.c_int32(-1)
     _check(_lib().pbicgstab_test_barrier_timeout(timeout_ms, extra_arrivals, C.byref(st)), "barrier test")

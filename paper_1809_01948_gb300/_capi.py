@@ -17,6 +17,7 @@ PREC_NONE, PREC_JACOBI, PREC_NEUMANN = 0, 1, 2
 FP64, MIXED = 0, 1
 PIPELINED, CLASSIC = 0, 1
 HIST_STRIDE = 8
+PROPAGATION_PRODUCTS = ("U", "OU", "BA", "UEA", "BAEA", "BPA", "UC", "BAC", "BD")
 NOALLOC_MAX_N = 32768
 NOALLOC_MAX_VALUES = 524288
 
@@ -86,6 +87,7 @@ PROTOTYPES = {
     "pbicgstab_batch_destroy": (C.c_int, [C.c_void_p]),
     "pbicgstab_solve_batched": (C.c_int, [C.POINTER(Batch), C.POINTER(Options), C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.POINTER(BatchResult)]),
+    "pbicgstab_propagation_norms": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
