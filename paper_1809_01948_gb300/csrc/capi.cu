@@ -303,8 +303,11 @@ static const void* kernel_ptr(const pbcg_options& o) {
   return o.rr_auto ? (const void*)pbicgstab_kernel<T, true> : (const void*)pbicgstab_kernel<T, false>;
 }
 
+// Default shape: one 1024-thread block per SM (32 warps, the register limit of the
+// solver kernels); measured faster than two 512-thread blocks per SM on the 2D and 3D
+// convection-diffusion systems (fewer blocks at each grid barrier and reduction).
 static int kernel_threads(const pbcg_ctx* c) {
-  return c->opt.block_threads ? c->opt.block_threads : 512;
+  return c->opt.block_threads ? c->opt.block_threads : 1024;
 }
 
 pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads) {
@@ -317,7 +320,7 @@ pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads) {
   if (max_coresident <= 0) return set_error(PBCG_INVALID_ARG, "kernel cannot be resident with %d threads per block", nt);
   int g = c->opt.grid_blocks;
   if (g == 0) {
-    // every SM busy (up to 2 blocks per SM), but at least 32 rows per block
+    // every SM busy (up to 2 co-resident blocks per SM), but at least 32 rows per block
     const long long want = (c->n + 31) / 32;
     g = (int)std::min<long long>(std::max<long long>(1, want), (long long)std::min(max_coresident, 2 * sms));
   }
