@@ -32,7 +32,11 @@ GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations_convdiff
 
 
 # ----------------------------------------------------------------------------- byte model
-def bytes_per_row_iteration(precision: str, fmt: str = "dia", ndiag: int = 5, nnz_row: float = 5.0) -> float:
+MASK_BYTES = 2   # stencil storage: one 16-bit presence mask per row and SpMV
+
+
+def bytes_per_row_iteration(precision: str, fmt: str = "dia", ndiag: int = 5, nnz_row: float = 5.0,
+                            storage: str = "stencil") -> float:
     """Algorithmic bytes per row and iteration of the fused two-pass iteration
     (Jacobi folded into the operator A D^{-1}, m and n formed on the fly, q, u, y
     recomputed, neighbour gathers counted once):
@@ -40,34 +44,42 @@ def bytes_per_row_iteration(precision: str, fmt: str = "dia", ndiag: int = 5, nn
       pass B reads z x g k l r s w t r0 + D^{-1}, writes v x r k w;
     28 vector streams (x read+written in FP64) plus two reads of the operator.
     DIA: the folded operator stores ndiag-1 diagonals and D^{-1} replaces the unit
-    main diagonal, so operator + D^{-1} = ndiag values per row per pass."""
+    main diagonal, so operator + D^{-1} = ndiag values per row per pass.  Stencil
+    storage: the operator is the per-row mask and D^{-1} one constant."""
     es = 8 if precision == "fp64" else 4
     vec = 26 * es + 2 * 8            # x is FP64 in both modes
-    if fmt == "dia":
+    if storage == "stencil":
+        mat = 2 * MASK_BYTES
+    elif fmt == "dia":
         mat = 2 * ndiag * es
     else:
         mat = 2 * (nnz_row * (es + 4) + 4 + es)   # values + col + row_ptr + D^{-1}
     return float(vec + mat)
 
 
-def bytes_per_row_iteration_neumann(precision: str, degree: int = 2, nnz_row: float = 7.0) -> float:
+def bytes_per_row_iteration_neumann(precision: str, degree: int = 2, nnz_row: float = 7.0,
+                                    storage: str = "stencil") -> float:
     """Algorithmic bytes per row and iteration with a degree-d Neumann preconditioner on a
     CSR matrix: m and n must be stored, each M^{-1} application adds d Jacobi sweeps, so
     the iteration streams 30 + 8d vectors (x in FP64) and reads the matrix 2 + 2d times
-    (values + int32 columns + row pointer).  Degree 2: 46 streams + 6 matrix reads."""
+    (values + int32 columns + row pointer; stencil storage: the mask).  Degree 2:
+    46 streams + 6 matrix reads."""
     es = 8 if precision == "fp64" else 4
     streams = 30 + 8 * degree
     vec = (streams - 2) * es + 2 * 8
-    mat = (2 + 2 * degree) * (nnz_row * (es + 4) + 4)
+    per_read = MASK_BYTES if storage == "stencil" else nnz_row * (es + 4) + 4
+    mat = (2 + 2 * degree) * per_read
     return float(vec + mat)
 
 
-def bytes_per_row_replacement(precision: str, ndiag: int = 5) -> float:
+def bytes_per_row_replacement(precision: str, ndiag: int = 5, storage: str = "stencil") -> float:
     """Eq. (rr) pass pair: R1 reads b, x, g, z + 2 FP64 operator reads, writes r k s l n;
     R2 reads r, s, r0 + 2 folded operator reads, writes w z."""
     es = 8 if precision == "fp64" else 4
-    r1 = 2 * 8 + es * 2 + 2 * ndiag * 8 + 5 * es
-    r2 = 3 * es + 2 * ndiag * es + 2 * es
+    op64 = MASK_BYTES if storage == "stencil" else ndiag * 8
+    opT = MASK_BYTES if storage == "stencil" else ndiag * es
+    r1 = 2 * 8 + es * 2 + 2 * op64 + 5 * es
+    r2 = 3 * es + 2 * opT + 2 * es
     return float(r1 + r2)
 
 
@@ -79,10 +91,20 @@ def fp64_flops_per_row_iteration(ndiag: int = 5) -> float:
     return 2 * 2 * (ndiag - 1) + 2 + 2 * 18 + 2 * 7
 
 
+def fp64_flops_per_row_iteration_neumann(nnz_row: int = 7, degree: int = 2) -> float:
+    """The same count with a degree-d Neumann preconditioner on a CSR operator (diagonal
+    stored): t = A m and v = A n (nnz_row FMAs each); each M^{-1} application runs d Jacobi
+    sweeps of one SpMV plus 3 flops (subtract, FMA) -- the first also scales by D^{-1} --
+    for m and for n; the AXPYs (18) and 7 dot products as above."""
+    spmv = 2 * nnz_row
+    sweeps = 2 * (degree * (spmv + 3) + 1)
+    return 2 * spmv + sweeps + 2 * 18 + 2 * 7
+
+
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("common.cuh", "solver.cuh", "capi.cu"):
+    for f in ("common.cuh", "solver.cuh", "capi.cu", "capi_internal.h", "stencil.cu"):
         h.update(open(os.path.join(ROOT, "paper_1809_01948_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -184,7 +206,11 @@ def run_gpu(args):
         # Algorithm 1, the paper's reference method, on the same system (three reduction
         # phases per iteration instead of two)
         variants["classic"] = dict(precision="fp64", method="classic", rr_period=0, rr_theta=0.0)
+    # the headline variant with the matrix values kept as given (CSR / DIA) instead of the
+    # constant-coefficient stencil storage the library selects for these operators
+    variants[args.precision + "_general"] = dict(variants[args.precision], operator_storage="general")
     solvers = {k: pb.Solver(n, tol=1e-10, max_it=args.max_it, **mat, **v) for k, v in variants.items()}
+    storage = solvers[args.precision].storage
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
@@ -250,8 +276,9 @@ def run_gpu(args):
 
     # roofline of the dominant kernel (the persistent solver), per launch
     prec = args.precision
-    bpr = bytes_per_row_iteration(prec) if args.workload == "c2" else bytes_per_row_iteration_neumann(prec)
-    alg_bytes = n * (bpr * head["iterations"] + bytes_per_row_replacement(prec) * head["n_replacements"])
+    bpr = (bytes_per_row_iteration(prec, storage=storage) if args.workload == "c2"
+           else bytes_per_row_iteration_neumann(prec, storage=storage))
+    alg_bytes = n * (bpr * head["iterations"] + bytes_per_row_replacement(prec, storage=storage) * head["n_replacements"])
     kernel_s = head["kernel_ms"] * 1e-3
     peaks = {}
     try:
@@ -265,21 +292,21 @@ def run_gpu(args):
            "frac": round(alg_bytes / kernel_s / 1e9 / hbm_peak, 4),
            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
            "bytes_per_row_iteration": bpr}
-    if prec == "fp64" and args.workload == "c2":
-        # FP64 pipe bound: GB300 runs FP64 at 1/58 of FP32; nominal 1.25 TFLOP/s (measured 1.197)
-        flops = fp64_flops_per_row_iteration() * n * head["iterations"]
-        ach = flops / kernel_s / 1e12
+    if prec == "fp64":
+        # FP64 pipe bound: GB300 runs FP64 at 1/58 of FP32; nominal 1.25 TFLOP/s (measured DFMA 1.197)
+        fpr = fp64_flops_per_row_iteration() if args.workload == "c2" else fp64_flops_per_row_iteration_neumann()
+        ach = fpr * n * head["iterations"] / kernel_s / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": 1.25, "unit": "TFLOP/s",
                 "frac": round(ach / 1.25, 4), "traffic": traffic,
                 "peak_source": "nominal FP64 rate of the profiling recipe (measured DFMA: 1.197)",
-                "flops_per_row_iteration": fp64_flops_per_row_iteration(), "hbm": hbm}
+                "flops_per_row_iteration": fpr, "hbm": hbm}
     else:
         roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm["frac"], "traffic": traffic, "peak_source": hbm["peak_source"],
                 "bytes_per_row_iteration": bpr,
                 }
         if args.workload == "c2":
-            roof["note"] = "working set is L2-resident across iterations (DRAM traffic ~7 B/row/it)"
+            roof["note"] = "working set is L2-resident across iterations (DRAM traffic ~3 B/row/it)"
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and args.workload == "c2":
@@ -293,6 +320,8 @@ def run_gpu(args):
             "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
             "config": {"workload": workload, "n": n,
                        "format": "DIA 5 diagonals FP64" if args.workload == "c2" else "CSR int32, 7 nnz/row, FP64 values",
+                       "operator_storage": storage + (" (constant coefficients detected at create: one value per "
+                                                      "offset + 16-bit row mask)" if storage == "stencil" else ""),
                        "precision": prec, "replacement": variants[prec], "global_batch": 1 * world,
                        "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps (256 MB write)"},
             "iterations": head["iterations"], "n_replacements": head["n_replacements"],

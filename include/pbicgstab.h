@@ -55,6 +55,13 @@ typedef enum pbcg_precision {
                               b, dot-product results, alpha/beta/omega and replacement
                               residual r = b - A x (FP64 values)                          */
 } pbcg_precision;
+typedef enum pbcg_storage {
+  PBCG_STORAGE_AUTO = 0,    /* option: keep a constant-coefficient stencil as one value per
+                               offset plus a 16-bit presence mask per row (see
+                               pbicgstab_operator_storage), other matrices as given      */
+  PBCG_STORAGE_GENERAL = 1, /* option and query: the CSR / DIA values as given          */
+  PBCG_STORAGE_STENCIL = 2  /* query only: the context uses the stencil form             */
+} pbcg_storage;
 typedef enum pbcg_method {
   PBCG_PIPELINED = 0,      /* Algorithm 2 (p-BiCGStab), two grid-wide reduction phases per
                               iteration, with the replacement policies of the options    */
@@ -120,6 +127,9 @@ typedef struct pbcg_options {
                               PBCG_CLASSIC (Algorithm 1: FP64 only, no or Jacobi
                               preconditioning, no replacement, no restarts)             */
   double rr_tau;           /* tau of Eq. (criterion); <= 0: sqrt(2^-52)               */
+  int32_t operator_storage;/* pbcg_storage: PBCG_STORAGE_AUTO (default) or _GENERAL; fixed
+                              at create                                                 */
+  int32_t reserved2;
 } pbcg_options;
 
 typedef struct pbcg_result {
@@ -149,8 +159,8 @@ pbcg_status pbicgstab_create(pbcg_ctx** out, const pbcg_matrix* A, const pbcg_pr
                              const pbcg_options* opt, void* stream);
 
 /* Replace the solve options (tolerance, iteration limit, replacement policy,
- * history buffers, launch shape) of an existing context.  The precision cannot
- * change.  ctx, opt: host, non-NULL. */
+ * history buffers, launch shape) of an existing context.  The precision and the
+ * operator storage cannot change.  ctx, opt: host, non-NULL. */
 pbcg_status pbicgstab_set_options(pbcg_ctx* ctx, const pbcg_options* opt);
 
 /* Solve A x = b with p-BiCGStab (Algorithm 2 with Eq. rr replacements per the
@@ -302,6 +312,14 @@ pbcg_status pbicgstab_solve_batched(const pbcg_batch* batch, const pbcg_options*
 #define PBCG_NOALLOC_MAX_VALUES 524288
 pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_precond* M, const pbcg_options* opt,
                                     const double* b, double* x, pbcg_result* res, void* stream);
+
+/* How the context stores A: PBCG_STORAGE_STENCIL when options.operator_storage was
+ * PBCG_STORAGE_AUTO and A is a constant-coefficient stencil -- at most 16 distinct
+ * offsets col - row among its non-zero entries, one value per offset and, with a
+ * preconditioner, a constant diagonal -- else PBCG_STORAGE_GENERAL.  The stencil form
+ * computes the same products in the same order (every SpMV sums in ascending column
+ * order).  ctx, storage: host, non-NULL. */
+pbcg_status pbicgstab_operator_storage(const pbcg_ctx* ctx, int32_t* storage);
 
 /* Error propagation diagnostics (Section 2.4): column max-norms of the nine products
  * of Eq. (all_error_matrices), U, OU, BA, UEA, BAEA, BPA, UC, BAC, BD, formed from the

@@ -50,6 +50,7 @@ def _stream_handle(stream: Optional[torch.cuda.Stream]):
 _PREC = {"none": capi.PREC_NONE, "jacobi": capi.PREC_JACOBI, "neumann": capi.PREC_NEUMANN}
 _PRECISION = {"fp64": capi.FP64, "mixed": capi.MIXED}
 _METHOD = {"pipelined": capi.PIPELINED, "classic": capi.CLASSIC}
+_STORAGE = {"auto": capi.STORAGE_AUTO, "general": capi.STORAGE_GENERAL}
 
 
 class Solver:
@@ -65,7 +66,7 @@ class Solver:
                  precision: str = "fp64", tol: float = 1e-10, max_it: int = 10000, rr_period: int = 0,
                  rr_theta: float = 0.0, timeout_ms: float = 2000.0, grid_blocks: int = 0,
                  block_threads: int = 0, max_restarts: int = 0, rr_auto: bool = False, rr_tau: float = 0.0,
-                 method: str = "pipelined", stream: Optional[torch.cuda.Stream] = None):
+                 method: str = "pipelined", operator_storage: str = "auto", stream: Optional[torch.cuda.Stream] = None):
         lib = _lib()
         self.n = int(n)
         self.stream = stream
@@ -112,6 +113,7 @@ class Solver:
         self.opt.rr_auto = int(bool(rr_auto))
         self.opt.rr_tau = rr_tau
         self.opt.method = _METHOD[method]
+        self.opt.operator_storage = _STORAGE[operator_storage]
         self.ctx = C.c_void_p()
         _check(lib.pbicgstab_create(C.byref(self.ctx), C.byref(m), C.byref(p), C.byref(self.opt),
                                     _stream_handle(stream)), "pbicgstab_create")
@@ -126,6 +128,8 @@ class Solver:
                 v = _PRECISION[v]
             elif k == "method":
                 v = _METHOD[v]
+            elif k == "operator_storage":
+                v = _STORAGE[v]
             setattr(self.opt, k, v)
         self.opt.hist_x = _ptr(hist_x) if hist_x is not None else None
         self.opt.hist_scalars = _ptr(hist_scalars) if hist_scalars is not None else None
@@ -177,6 +181,13 @@ class Solver:
         if st in (capi.PBCG_INVALID_ARG, capi.PBCG_CUDA_ERROR, capi.PBCG_OUT_OF_MEMORY, capi.PBCG_TIMEOUT):
             raise PBCGError(st, capi.last_error())
         return Xc.t(), list(res)
+
+    @property
+    def storage(self) -> str:
+        """"stencil" when the context keeps A as a constant-coefficient stencil, else "general"."""
+        v = C.c_int32(-1)
+        _check(_lib().pbicgstab_operator_storage(self.ctx, C.byref(v)), "pbicgstab_operator_storage")
+        return "stencil" if v.value == capi.STORAGE_STENCIL else "general"
 
     def transpose(self) -> "Solver":
         """A context for A^T (``pbicgstab_create_transpose``), same preconditioner and options."""

@@ -16,6 +16,7 @@ F64, F32 = 0, 1
 PREC_NONE, PREC_JACOBI, PREC_NEUMANN = 0, 1, 2
 FP64, MIXED = 0, 1
 PIPELINED, CLASSIC = 0, 1
+STORAGE_AUTO, STORAGE_GENERAL, STORAGE_STENCIL = 0, 1, 2
 HIST_STRIDE = 8
 PROPAGATION_PRODUCTS = ("U", "OU", "BA", "UEA", "BAEA", "BPA", "UC", "BAC", "BD")
 NOALLOC_MAX_N = 32768
@@ -38,7 +39,8 @@ class Options(C.Structure):
                 ("timeout_ms", C.c_double), ("record_iterates", C.c_int32), ("hist_len", C.c_int32),
                 ("hist_x", C.c_void_p), ("hist_scalars", C.c_void_p),
                 ("grid_blocks", C.c_int32), ("block_threads", C.c_int32),
-                ("max_restarts", C.c_int32), ("method", C.c_int32), ("rr_tau", C.c_double)]
+                ("max_restarts", C.c_int32), ("method", C.c_int32), ("rr_tau", C.c_double),
+                ("operator_storage", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -88,6 +90,7 @@ PROTOTYPES = {
     "pbicgstab_solve_batched": (C.c_int, [C.POINTER(Batch), C.POINTER(Options), C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.POINTER(BatchResult)]),
     "pbicgstab_propagation_norms": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pbicgstab_operator_storage": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
 }
 
 _lib = None

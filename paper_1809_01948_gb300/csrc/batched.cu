@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev 
       p.Au = csr_view<T>(n, rp, col, (const T*)d.valAu + e0);
       p.A64 = csr_view<VR>(n, rp, col, (const VR*)d.valR + e0);
       p.dinv = d.dinv ? (const T*)d.dinv + r0 : nullptr;
+      p.dinv_c = T(0);
       p.prec = d.prec;
       p.degree = 0;
       p.b = d.b + r0;

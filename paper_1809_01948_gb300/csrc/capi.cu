@@ -246,7 +246,7 @@ __global__ void barrier_timeout_kernel(unsigned* counter, int* err, int extra, u
 static void free_ctx(pbcg_ctx* c) {
   if (!c) return;
   if (c->valAu && c->valAu != (void*)c->val64) cudaFree(c->valAu);
-  void* ptrs[] = {c->row_ptr, c->col, c->val64, c->valAt, c->diag64, c->dinv64, c->dinvT,
+  void* ptrs[] = {c->row_ptr, c->col, c->val64, c->valAt, c->diag64, c->dinv64, c->dinvT, c->st_mask,
                   c->vecs, c->part, c->dstate, c->multi_vecs, c->multi_part, c->multi_state, c->multi_params};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -275,6 +275,8 @@ pbcg_status check_options(const pbcg_options* o, long long n) {
     return set_error(PBCG_INVALID_ARG, "options.block_threads must be 0 or a multiple of 32 in [32, 1024]");
   if (o->grid_blocks < 0) return set_error(PBCG_INVALID_ARG, "options.grid_blocks must be >= 0");
   if (o->max_restarts < 0 || o->max_restarts > 1000) return set_error(PBCG_INVALID_ARG, "options.max_restarts must be in [0, 1000]");
+  if (o->operator_storage != PBCG_STORAGE_AUTO && o->operator_storage != PBCG_STORAGE_GENERAL)
+    return set_error(PBCG_INVALID_ARG, "options.operator_storage must be PBCG_STORAGE_AUTO or PBCG_STORAGE_GENERAL");
   if (o->method != PBCG_PIPELINED && o->method != PBCG_CLASSIC)
     return set_error(PBCG_INVALID_ARG, "options.method must be PBCG_PIPELINED or PBCG_CLASSIC");
   if (o->method == PBCG_CLASSIC) {
@@ -461,6 +463,7 @@ static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
     c->norm_bound = std::sqrt(colmax * rowmax);
     c->dinv_max = need_diag ? dmax : 1.0;
   }
+  if (c->opt.operator_storage == PBCG_STORAGE_AUTO) return build_stencil(c);
   return PBCG_OK;
 }
 
@@ -532,6 +535,8 @@ extern "C" pbcg_status pbicgstab_set_options(pbcg_ctx* c, const pbcg_options* op
   pbcg_status st = check_options(opt, c->n);
   if (st != PBCG_OK) return st;
   if (opt->precision != c->precision) return set_error(PBCG_INVALID_ARG, "precision cannot change after create");
+  if (opt->operator_storage != c->opt.operator_storage)
+    return set_error(PBCG_INVALID_ARG, "operator_storage cannot change after create");
   st = check_method_precond(opt, c->prec_kind);
   if (st != PBCG_OK) return st;
   c->opt = *opt;

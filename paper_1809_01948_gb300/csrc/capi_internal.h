@@ -62,6 +62,15 @@ struct pbcg_ctx {
   int at_unit_diag = 0;
   int bandwidth = 0;         // max |col - row| over the stored entries
   int maxnnz = 0;            // max stored entries in a row
+  // constant-coefficient stencil form of A (options.operator_storage auto, when every
+  // offset carries one value and the diagonal is constant): views use these instead of
+  // the stored values
+  int stencil = 0;
+  int st_n = 0;                          // offsets, ascending
+  int st_off[kMaxDiag] = {0};
+  double st_val[kMaxDiag] = {0};         // A's value at each offset
+  double st_dinv = 0.0;                  // 1 / (the constant diagonal)
+  unsigned short* st_mask = nullptr;     // per row: bit d set when the entry at st_off[d] is present
   double norm_bound = 0.0;   // sqrt(||A||_1 ||A||_inf) (upper bound of ||A||_2)
   double dinv_max = 1.0;     // max |d_inv| in the working precision (1 without preconditioner)
   // vectors + reductions
@@ -84,8 +93,32 @@ struct pbcg_ctx {
 
 inline size_t elem_size(int precision) { return precision == PBCG_MIXED ? sizeof(float) : sizeof(double); }
 
+// Stencil view of A (hot = false: values of A rounded to V) or of the Jacobi-folded
+// operator A D^{-1} (hot = true: a_ij * d_inv rounded once to V, as the fold kernels
+// compute it; the DIA fold's unit main diagonal is implicit, the CSR fold keeps it).
+template <typename V>
+inline MatView<V> make_stencil_view(const pbcg_ctx* c, bool hot) {
+  MatView<V> m;
+  memset(&m, 0, sizeof m);
+  m.fmt = 2;
+  m.n = c->n;
+  m.mask = c->st_mask;
+  int k = 0;
+  for (int d = 0; d < c->st_n; ++d) {
+    if (hot && c->fmt == PBCG_FMT_DIA && c->st_off[d] == 0) continue;
+    m.off[k] = c->st_off[d];
+    m.cval[k] = hot ? V(c->st_val[d] * c->st_dinv) : V(c->st_val[d]);
+    m.mbit[k] = (unsigned char)d;
+    ++k;
+  }
+  m.ndiag = k;
+  m.unit_diag = (hot && c->fmt == PBCG_FMT_DIA) ? 1 : 0;
+  return m;
+}
+
 template <typename V>
 inline MatView<V> make_view(const pbcg_ctx* c, const V* val, bool hot) {
+  if (c->stencil) return make_stencil_view<V>(c, hot);
   MatView<V> m;
   memset(&m, 0, sizeof m);
   m.fmt = c->fmt;
@@ -110,6 +143,7 @@ inline MatView<double> pbcg_view64(const pbcg_ctx* c) { return make_view<double>
 
 
 pbcg_status check_options(const pbcg_options* o, long long n);
+pbcg_status build_stencil(pbcg_ctx* c);
 pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads);
 pbcg_status enqueue_true_residual(pbcg_ctx* c, const double* b, const double* x, double* out_dev);
 
@@ -125,8 +159,9 @@ inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int 
   if (!c->valAt && c->fmt == PBCG_FMT_DIA) p.At = make_view<T>(c, at, false);
   p.Au = make_view<T>(c, (const T*)c->valAu, false);
   p.A64 = make_view<double>(c, c->val64, false);
-  p.dinv = c->prec_kind == PBCG_PREC_NONE ? nullptr
+  p.dinv = (c->prec_kind == PBCG_PREC_NONE || c->stencil) ? nullptr
            : (std::is_same<T, float>::value ? (const T*)c->dinvT : (const T*)c->dinv64);
+  p.dinv_c = T(c->st_dinv);
   p.prec = c->prec_kind;
   p.degree = c->degree;
   p.b = b;

@@ -18,19 +18,26 @@ enum DevStatus : int {
 };
 
 // ---------------------------------------------------------------- matrices
-// A CSR matrix (row_ptr/col int32) or a DIA matrix (ndiag diagonals, diagonal-major
-// values, val[d*n + i] = A[i, i+off[d]]).  For the operator A D^{-1} of the Jacobi
-// fold, DIA drops its main diagonal (whose exact value is 1) and sets unit_diag.
+// A CSR matrix (row_ptr/col int32), a DIA matrix (ndiag diagonals, diagonal-major
+// values, val[d*n + i] = A[i, i+off[d]]) or a constant-coefficient stencil: one value
+// per offset (cval[d]) and a per-row presence mask (bit mbit[d] of mask[i] set when row
+// i has its entry at offset off[d]), which is what a structured-grid operator with
+// constant coefficients reduces to -- 2 bytes per row instead of its values.  For the
+// operator A D^{-1} of the Jacobi fold, DIA drops its main diagonal (whose exact value
+// is 1) and sets unit_diag.
 template <typename V>
 struct MatView {
-  int fmt;          // 0 CSR, 1 DIA
+  int fmt;          // 0 CSR, 1 DIA, 2 stencil
   int n;
   const int* __restrict__ row_ptr;
   const int* __restrict__ col;
   const V* __restrict__ val;
+  const unsigned short* __restrict__ mask;   // stencil: presence bits per row
   int ndiag;
-  int unit_diag;    // DIA: add x[i] (exact unit main diagonal) before the stored diagonals
+  int unit_diag;    // DIA / stencil: add x[i] (exact unit main diagonal) before the others
   int off[kMaxDiag];
+  V cval[kMaxDiag];                 // stencil: the value at offset off[d]
+  unsigned char mbit[kMaxDiag];     // stencil: mask bit of offset off[d]
 };
 
 // y_i = sum_j a_ij x_j for one row i, accumulated with FMA in type Acc, stored
@@ -43,7 +50,7 @@ __device__ __forceinline__ Acc row_dot(const MatView<V>& A, const X* __restrict_
     for (int e = e0; e < e1; ++e) {
       acc = fma(Acc(__ldg(A.val + e)), Acc(x[__ldg(A.col + e)]), acc);
     }
-  } else {
+  } else if (A.fmt == 1) {
     if (A.unit_diag) acc = Acc(x[i]);
     const int n = A.n;
 #pragma unroll 4
@@ -51,6 +58,12 @@ __device__ __forceinline__ Acc row_dot(const MatView<V>& A, const X* __restrict_
       const int j = i + A.off[d];
       if (j >= 0 && j < n) acc = fma(Acc(__ldg(A.val + (size_t)d * n + i)), Acc(x[j]), acc);
     }
+  } else {
+    const unsigned msk = __ldg(A.mask + i);
+    if (A.unit_diag) acc = Acc(x[i]);
+#pragma unroll 4
+    for (int d = 0; d < A.ndiag; ++d)
+      if ((msk >> A.mbit[d]) & 1u) acc = fma(Acc(A.cval[d]), Acc(x[i + A.off[d]]), acc);
   }
   return acc;
 }
@@ -64,7 +77,7 @@ __device__ __forceinline__ Acc row_dot_fn(const MatView<V>& A, int i, F xj) {
   if (A.fmt == 0) {
     const int e0 = __ldg(A.row_ptr + i), e1 = __ldg(A.row_ptr + i + 1);
     for (int e = e0; e < e1; ++e) acc = fma(Acc(__ldg(A.val + e)), Acc(xj(__ldg(A.col + e))), acc);
-  } else {
+  } else if (A.fmt == 1) {
     if (A.unit_diag) acc = Acc(xj(i));
     const int n = A.n;
 #pragma unroll 4
@@ -72,6 +85,12 @@ __device__ __forceinline__ Acc row_dot_fn(const MatView<V>& A, int i, F xj) {
       const int j = i + A.off[d];
       if (j >= 0 && j < n) acc = fma(Acc(__ldg(A.val + (size_t)d * n + i)), Acc(xj(j)), acc);
     }
+  } else {
+    const unsigned msk = __ldg(A.mask + i);
+    if (A.unit_diag) acc = Acc(xj(i));
+#pragma unroll 4
+    for (int d = 0; d < A.ndiag; ++d)
+      if ((msk >> A.mbit[d]) & 1u) acc = fma(Acc(A.cval[d]), Acc(xj(i + A.off[d])), acc);
   }
   return acc;
 }

@@ -44,7 +44,8 @@ struct SolverParams {
   MatView<T> Au;        // A in the vector precision (Neumann sweeps, t = A m, v = A n)
   MatView<VR> A64;      // A with its stored values (FP64, or FP32 widened exactly): initial
                         // and replacement residuals, evaluated in FP64
-  const T* dinv;        // D^{-1} (nullptr without preconditioner)
+  const T* dinv;        // D^{-1} (nullptr without preconditioner or when D is constant)
+  T dinv_c;             // D^{-1} of a constant diagonal (used when dinv is nullptr)
   int prec;             // 0 none, 1 Jacobi, 2 Neumann
   int degree;
   const double* b;
@@ -217,9 +218,15 @@ struct BlockTeam {
   __device__ __forceinline__ bool leader() const { return threadIdx.x == 0; }
 };
 
+// d_inv of row i: the stored vector, or the one value of a constant diagonal.
+template <typename T, typename VR>
+__device__ __forceinline__ T dinv_at(const SolverParams<T, VR>& p, int i) {
+  return p.dinv ? __ldg(p.dinv + i) : p.dinv_c;
+}
+
 template <typename T, typename VR>
 __device__ __forceinline__ T minv_local(const SolverParams<T, VR>& p, T v, int i) {
-  return p.prec == 1 ? T(__ldg(p.dinv + i) * v) : v;
+  return p.prec == 1 ? T(dinv_at(p, i) * v) : v;
 }
 
 // Neumann polynomial M^{-1} src = sum_{j<=d} (I - D^{-1}A)^j D^{-1} src by d
@@ -237,7 +244,7 @@ __device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T*
     T* out0 = ((d - j) % 2 == 0) ? dst0 : p.tmpa;
     T* out1 = ((d - j) % 2 == 0) ? dst1 : p.tmpb;
     for (int i = row0 + threadIdx.x; i < row1; i += rstride) {
-      const T di = __ldg(p.dinv + i);
+      const T di = dinv_at(p, i);
       {
         const T sv = src0[i];
         if (j == 1) out0[i] = fma(di, sv - row_dot<T>(p.At, src0, i), di * sv);

@@ -1,0 +1,93 @@
+"""The constant-coefficient stencil storage of the operator (options.operator_storage):
+which matrices qualify, and that solves and SpMVs with it equal the general CSR / DIA
+storage bit for bit (same products, same ascending-offset order)."""
+import numpy as np
+import pytest
+
+import testproblems as tp
+from gpu_common import gpu_solve, make_solver, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _variable_coefficients(prob, seed=3):
+    """The same sparsity, one coupling changed by a relative 1e-3: not a stencil."""
+    A = prob.A
+    val = A.val.copy()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    e = int(rng.integers(0, A.nnz))
+    while A.col[e] == np.searchsorted(A.row_ptr, e, side="right") - 1:   # an off-diagonal entry
+        e = int(rng.integers(0, A.nnz))
+    val[e] *= 1.001
+    B = tp.CSR(A.n, A.row_ptr.copy(), A.col.copy(), val)
+    return tp.Problem(prob.name + "_var", B, tp.problems._spmv(B, prob.x_star), prob.x0, prob.x_star,
+                      precond=prob.precond, degree=prob.degree, fmt=prob.fmt)
+
+
+def test_detection():
+    torch_cuda()
+    assert make_solver(tp.config1(30), fmt="csr", precond="none").storage == "stencil"
+    assert make_solver(tp.config2(40), fmt="dia").storage == "stencil"
+    assert make_solver(tp.config2(40), fmt="csr").storage == "stencil"
+    assert make_solver(tp.config3(10), fmt="csr").storage == "stencil"
+    T2 = tp.tp2(20)
+    p2 = tp.Problem("tp2", T2, np.ones(T2.n), np.zeros(T2.n), None, precond="jacobi", fmt="csr")
+    assert make_solver(p2).storage == "stencil"
+    assert make_solver(tp.config2(40), fmt="dia", operator_storage="general").storage == "general"
+    var = _variable_coefficients(tp.config2(40))
+    assert make_solver(var, fmt="csr").storage == "general"
+    assert make_solver(var, fmt="dia").storage == "general"
+    rng = np.random.Generator(np.random.PCG64(9))
+    A = tp.random_banded_system(3000, rng)
+    rb = tp.Problem("rb", A, np.ones(A.n), np.zeros(A.n), None, precond="jacobi", fmt="csr")
+    assert make_solver(rb).storage == "general"
+
+
+CASES = {
+    "poisson_csr_none": (lambda: tp.config1(60), "csr", "fp64", "pipelined", dict()),
+    "convdiff2d_dia_jacobi": (lambda: tp.config2(96), "dia", "fp64", "pipelined", dict(rr_period=50)),
+    "convdiff2d_csr_jacobi_mixed": (lambda: tp.config2(64), "csr", "mixed", "pipelined", dict(rr_theta=1e-3)),
+    "convdiff3d_csr_neumann": (lambda: tp.config3(20), "csr", "fp64", "pipelined", dict(rr_period=50)),
+    "convdiff3d_csr_neumann_mixed": (lambda: tp.config3(20), "csr", "mixed", "pipelined", dict(rr_theta=3e-3)),
+    "convdiff2d_dia_classic": (lambda: tp.config2(96), "dia", "fp64", "classic", dict()),
+    "convdiff2d_dia_auto_rr": (lambda: tp.config2(64), "dia", "fp64", "pipelined", dict(rr_auto=True)),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solves_bitwise_equal_to_general_storage(name):
+    maker, fmt, precision, method, kw = CASES[name]
+    prob = maker()
+    out = []
+    for storage in ("auto", "general"):
+        s = make_solver(prob, fmt=fmt, precision=precision, method=method, tol=1e-10, max_it=3000,
+                        operator_storage=storage, **kw)
+        assert s.storage == ("stencil" if storage == "auto" else "general")
+        x, res, its, hist = gpu_solve(s, prob.b, K=5, hist_len=50)
+        out.append((x, res, its, hist))
+    (x1, r1, i1, h1), (x2, r2, i2, h2) = out
+    assert r1.status == r2.status and r1.iterations == r2.iterations and r1.n_replacements == r2.n_replacements
+    assert np.array_equal(x1, x2)
+    assert np.array_equal(i1, i2)
+    assert np.array_equal(h1, h2, equal_nan=True)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "dia"])
+def test_spmv_and_true_residual_equal(fmt):
+    torch = torch_cuda()
+    prob = tp.config2(50)
+    sa = make_solver(prob, fmt=fmt)
+    sg = make_solver(prob, fmt=fmt, operator_storage="general")
+    rng = np.random.Generator(np.random.PCG64(4))
+    x = torch.from_numpy(rng.standard_normal(prob.A.n)).cuda()
+    assert torch.equal(sa.spmv(x), sg.spmv(x))
+    b = torch.from_numpy(prob.b).cuda()
+    assert sa.true_residual(b, x) == sg.true_residual(b, x)
+
+
+def test_storage_fixed_at_create():
+    torch_cuda()
+    import paper_1809_01948_gb300 as pb
+    s = make_solver(tp.config2(20), fmt="dia")
+    with pytest.raises(pb.PBCGError):
+        s.set_options(operator_storage="general")

@@ -65,7 +65,7 @@ def test_noalloc_matches_context_solver_twice(name, maker, fmt, prec, kw):
                                  dict(row_ptr=torch.from_numpy(prob.A.row_ptr).to(dev),
                                       col=torch.from_numpy(prob.A.col).to(dev),
                                       val=torch.from_numpy(prob.A.val).to(dev))),
-                    precond=prec, precision="fp64", tol=tol, max_it=5000, **kw)
+                    precond=prec, precision="fp64", tol=tol, max_it=5000, block_threads=512, **kw)
     b = torch.from_numpy(prob.b).to(dev)
     x_ref, r_ref = ref.solve(b)
     x_ref = x_ref.cpu().numpy()
@@ -75,6 +75,7 @@ def test_noalloc_matches_context_solver_twice(name, maker, fmt, prec, kw):
     opt = capi.Options()
     lib.pbicgstab_default_options(C.byref(opt))
     opt.tol, opt.max_it = tol, 5000
+    opt.block_threads = 512   # the same launch shape as the context above (same reduction order)
     opt.rr_period = kw.get("rr_period", 0)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     for call in range(2):
