@@ -292,6 +292,14 @@ def run_gpu(args):
            "frac": round(alg_bytes / kernel_s / 1e9 / hbm_peak, 4),
            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
            "bytes_per_row_iteration": bpr}
+    # the same time against the byte model of the general (CSR / DIA values) storage, which
+    # the stencil storage undercuts: the effective bandwidth of the solve
+    gen = (bytes_per_row_iteration(prec, storage="general") if args.workload == "c2"
+           else bytes_per_row_iteration_neumann(prec, storage="general"))
+    gen_bytes = n * (gen * head["iterations"] + bytes_per_row_replacement(prec, storage="general") * head["n_replacements"])
+    hbm["general_storage_model"] = {"bytes_per_row_iteration": gen,
+                                    "effective_gbs": round(gen_bytes / kernel_s / 1e9, 1),
+                                    "frac": round(gen_bytes / kernel_s / 1e9 / hbm_peak, 4)}
     if prec == "fp64":
         # FP64 pipe bound: GB300 runs FP64 at 1/58 of FP32; nominal 1.25 TFLOP/s (measured DFMA 1.197)
         fpr = fp64_flops_per_row_iteration() if args.workload == "c2" else fp64_flops_per_row_iteration_neumann()
@@ -303,7 +311,7 @@ def run_gpu(args):
     else:
         roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm["frac"], "traffic": traffic, "peak_source": hbm["peak_source"],
-                "bytes_per_row_iteration": bpr,
+                "bytes_per_row_iteration": bpr, "general_storage_model": hbm["general_storage_model"],
                 }
         if args.workload == "c2":
             roof["note"] = "working set is L2-resident across iterations (DRAM traffic ~3 B/row/it)"

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev 
       p.A64 = csr_view<VR>(n, rp, col, (const VR*)d.valR + e0);
       p.dinv = d.dinv ? (const T*)d.dinv + r0 : nullptr;
       p.dinv_c = T(0);
+      p.prefetch = 0;
       p.prec = d.prec;
       p.degree = 0;
       p.b = d.b + r0;

@@ -43,6 +43,13 @@ int sm_count() {
 }
 }  // namespace pbcg
 
+int l2_bytes() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev);
+  return v > 0 ? v : 0;
+}
+
 #define CK(call, what)                                   \
   do {                                                   \
     pbcg_status st__ = cuda_status((call), (what));      \
@@ -89,22 +96,32 @@ __global__ void validate_csr_kernel(int n, long long nnz, const int* row_ptr, co
 // compared through their bit patterns, and column sums are accumulated in fixed point
 // (each |a_ij| rounded up to a multiple of maxabs * 2^-40) with integer atomics, so the
 // results do not depend on the order of the atomic operations.
+// Warp-wide maximum, then one atomic per warp (a single global address would otherwise
+// serialise an atomic per element).
+__device__ __forceinline__ void warp_atomic_max(unsigned long long* addr, unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  if ((threadIdx.x & 31) == 0 && v) atomicMax(addr, v);
+}
+
 __global__ void absmax_kernel(MatView<double> A, long long nval, unsigned long long* bits) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= nval) return;
-  const double v = fabs(A.val[e]);
-  if (v > 0.0) atomicMax(bits, (unsigned long long)__double_as_longlong(v));
+  const double v = e < nval ? fabs(A.val[e]) : 0.0;
+  warp_atomic_max(bits, v > 0.0 ? (unsigned long long)__double_as_longlong(v) : 0ull);
 }
 
 __global__ void row_col_sums_kernel(MatView<double> A, const unsigned long long* maxabs_bits, unsigned long long* rowmax_bits,
                                     unsigned long long* colsum) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.n) return;
   const double maxabs = __longlong_as_double((long long)*maxabs_bits);
-  if (!(maxabs > 0.0)) return;
+  if (!(maxabs > 0.0)) return;   // uniform across the grid
   const double scale = 1099511627776.0 / maxabs;   // 2^40 / maxabs
   double rs = 0.0;
-  if (A.fmt == 0) {
+  if (i >= A.n) {
+  } else if (A.fmt == 0) {
     for (int e = A.row_ptr[i]; e < A.row_ptr[i + 1]; ++e) {
       const double a = fabs(A.val[e]);
       rs += a;
@@ -119,18 +136,18 @@ __global__ void row_col_sums_kernel(MatView<double> A, const unsigned long long*
       atomicAdd(colsum + j, (unsigned long long)ceil(a * scale));
     }
   }
-  atomicMax(rowmax_bits, (unsigned long long)__double_as_longlong(rs));
+  warp_atomic_max(rowmax_bits, (unsigned long long)__double_as_longlong(rs));
 }
 
 __global__ void max_u64_kernel(int n, const unsigned long long* v, unsigned long long* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) atomicMax(out, v[i]);
+  warp_atomic_max(out, i < n ? v[i] : 0ull);
 }
 
 template <typename T>
 __global__ void dinv_max_kernel(int n, const T* dinv, unsigned long long* bits) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) atomicMax(bits, (unsigned long long)__double_as_longlong(fabs((double)dinv[i])));
+  warp_atomic_max(bits, i < n ? (unsigned long long)__double_as_longlong(fabs((double)dinv[i])) : 0ull);
 }
 
 __global__ void validate_dia_kernel(int n, int ndiag, MatView<double> offs_only, const void* val, int f32,
@@ -305,26 +322,32 @@ static const void* kernel_ptr(const pbcg_options& o) {
   return o.rr_auto ? (const void*)pbicgstab_kernel<T, true> : (const void*)pbicgstab_kernel<T, false>;
 }
 
-// Default shape: one 1024-thread block per SM (32 warps, the register limit of the
-// solver kernels); measured faster than two 512-thread blocks per SM on the 2D and 3D
-// convection-diffusion systems (fewer blocks at each grid barrier and reduction).
+// Default shape: the solver kernels' register budgets (SolverLaunch): FP64 one 1024-thread
+// block per SM (measured faster than two 512-thread blocks on the 2D and 3D
+// convection-diffusion systems: fewer blocks at each grid barrier and reduction), mixed
+// three 512-thread blocks per SM.
 static int kernel_threads(const pbcg_ctx* c) {
-  return c->opt.block_threads ? c->opt.block_threads : 1024;
+  if (c->opt.block_threads) return c->opt.block_threads;
+  return c->precision == PBCG_MIXED ? pbcg::SolverLaunch<float>::kThreads : pbcg::SolverLaunch<double>::kThreads;
 }
 
 pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads) {
   const int nt = kernel_threads(c);
   int per_sm = 0;
   const void* k = c->precision == PBCG_MIXED ? kernel_ptr<float>(c->opt) : kernel_ptr<double>(c->opt);
+  cudaFuncAttributes fa;
+  CK(cudaFuncGetAttributes(&fa, k), "kernel attributes");
+  if (nt > fa.maxThreadsPerBlock)
+    return set_error(PBCG_INVALID_ARG, "block_threads %d above this solver's limit of %d", nt, fa.maxThreadsPerBlock);
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, 0), "occupancy query");
   const int sms = sm_count();
   const int max_coresident = per_sm * sms;
   if (max_coresident <= 0) return set_error(PBCG_INVALID_ARG, "kernel cannot be resident with %d threads per block", nt);
   int g = c->opt.grid_blocks;
   if (g == 0) {
-    // every SM busy (up to 2 co-resident blocks per SM), but at least 32 rows per block
+    // every co-resident block slot busy, but at least 32 rows per block
     const long long want = (c->n + 31) / 32;
-    g = (int)std::min<long long>(std::max<long long>(1, want), (long long)std::min(max_coresident, 2 * sms));
+    g = (int)std::min<long long>(std::max<long long>(1, want), (long long)max_coresident);
   }
   if (g > max_coresident)
     return set_error(PBCG_INVALID_ARG, "grid_blocks %d exceeds the %d co-resident blocks", g, max_coresident);

@@ -147,6 +147,19 @@ pbcg_status build_stencil(pbcg_ctx* c);
 pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads);
 pbcg_status enqueue_true_residual(pbcg_ctx* c, const double* b, const double* x, double* out_dev);
 
+int l2_bytes();   // L2 size of the current device in bytes
+
+// Bytes an iteration streams repeatedly: the work vectors it touches (about 12), x, and
+// the operator (the stencil mask, or the stored values and indices).
+inline double hot_bytes(const pbcg_ctx* c) {
+  const double es = (double)elem_size(c->precision);
+  double op;
+  if (c->stencil) op = 2.0;
+  else if (c->fmt == PBCG_FMT_DIA) op = c->ndiag * es;
+  else op = (double)c->nnz / std::max(1, c->n) * (es + 4.0) + 4.0;
+  return (double)c->n * (12.0 * es + 16.0 + op);
+}
+
 template <typename T>
 inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int grid) {
   SolverParams<T> p;
@@ -185,6 +198,9 @@ inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int 
   p.timeout_ns = (unsigned long long)(tms * 1e6);
   p.max_restarts = c->opt.max_restarts;
   p.strided = c->bandwidth > p.chunk / 2 ? 1 : 0;
+  // stencil storage only: with CSR / DIA values the row products already keep several
+  // loads per row in flight (measured slower with the prefetch on the 3D CSR operator)
+  p.prefetch = (c->stencil && hot_bytes(c) > (double)l2_bytes()) ? 1 : 0;
   p.rr_tau = c->opt.rr_tau > 0.0 ? c->opt.rr_tau : 1.4901161193847656e-08;
   p.bnd_msn = (double)c->maxnnz * sqrt((double)n);
   p.bnd_tmsn = sqrt((double)n);

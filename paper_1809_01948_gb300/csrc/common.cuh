@@ -95,6 +95,13 @@ __device__ __forceinline__ Acc row_dot_fn(const MatView<V>& A, int i, F xj) {
   return acc;
 }
 
+// Hint: bring the 128-byte line holding *ptr into L2 (no register is written, so a
+// thread can request the next row's operands while it computes the current one).
+template <typename V>
+__device__ __forceinline__ void prefetch_l2(const V* ptr) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
 // ---------------------------------------------------------------- timing / sync
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

@@ -34,8 +34,12 @@ __device__ __forceinline__ void insert_offset(int* table, int* overflow, int o) 
   unsigned h = ((unsigned)o * 2654435761u) >> 27;   // 5 bits: slot in [0, 32)
   for (int probe = 0; probe < kSlots; ++probe) {
     const int slot = (int)((h + probe) & (kSlots - 1));
-    const int prev = atomicCAS(table + slot, INT_MIN, o);
-    if (prev == INT_MIN || prev == o) return;
+    const int cur = __ldcg(table + slot);   // most entries find their offset already there
+    if (cur == o) return;
+    if (cur == INT_MIN) {
+      const int prev = atomicCAS(table + slot, INT_MIN, o);
+      if (prev == INT_MIN || prev == o) return;
+    }
   }
   atomicOr(overflow, 1);
 }
@@ -57,10 +61,17 @@ struct Offsets {
 __global__ void stencil_scan_kernel(int n, int fmt, const int* row_ptr, const int* col, const double* val,
                                     Offsets dia, Offsets st, unsigned long long* vmin, unsigned long long* vmax,
                                     unsigned short* mask) {
+  // block-level min / max in shared memory, then one global atomic per block and offset
+  __shared__ unsigned long long smin[kMaxDiag], smax[kMaxDiag];
+  if (threadIdx.x < kMaxDiag) {
+    smin[threadIdx.x] = ~0ull;
+    smax[threadIdx.x] = 0ull;
+  }
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
   unsigned m = 0;
-  if (fmt == PBCG_FMT_CSR) {
+  if (i >= n) {
+  } else if (fmt == PBCG_FMT_CSR) {
     for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
       const double v = val[e];
       if (v == 0.0) continue;
@@ -69,8 +80,8 @@ __global__ void stencil_scan_kernel(int n, int fmt, const int* row_ptr, const in
       while (d < st.n && st.off[d] != o) ++d;   // present: the offsets came from these entries
       if (d == st.n) continue;
       m |= 1u << d;
-      atomicMin(vmin + d, ordered_bits(v));
-      atomicMax(vmax + d, ordered_bits(v));
+      atomicMin(smin + d, ordered_bits(v));
+      atomicMax(smax + d, ordered_bits(v));
     }
   } else {
     for (int d = 0; d < dia.n; ++d) {
@@ -79,11 +90,16 @@ __global__ void stencil_scan_kernel(int n, int fmt, const int* row_ptr, const in
       const double v = val[(size_t)d * n + i];
       if (v == 0.0) continue;
       m |= 1u << d;   // DIA: the stencil keeps the given offsets in their order
-      atomicMin(vmin + d, ordered_bits(v));
-      atomicMax(vmax + d, ordered_bits(v));
+      atomicMin(smin + d, ordered_bits(v));
+      atomicMax(smax + d, ordered_bits(v));
     }
   }
-  mask[i] = (unsigned short)m;
+  if (i < n) mask[i] = (unsigned short)m;
+  __syncthreads();
+  if (threadIdx.x < st.n) {
+    if (smin[threadIdx.x] != ~0ull) atomicMin(vmin + threadIdx.x, smin[threadIdx.x]);
+    if (smax[threadIdx.x] != 0ull) atomicMax(vmax + threadIdx.x, smax[threadIdx.x]);
+  }
 }
 
 double from_ordered(unsigned long long u) {
