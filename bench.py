@@ -389,6 +389,135 @@ def cpu_baseline(args, gpu_iterations: int, sample_iters: int = 40):
             "ms_per_iteration": round(per_it * 1e3, 3)}
 
 
+# ----------------------------------------------------------------------------- batched and autograd
+def _timed_steps(args, one, sampler_on=True):
+    """W warm-up steps, then K timed steps bracketed by synchronisation; returns (ms list, clocks)."""
+    import torch
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    sampler = ClockSampler() if sampler_on else None
+    if sampler:
+        sampler.start()
+    out = []
+    for _ in range(args.steps):
+        out.append(one())
+    torch.cuda.synchronize()
+    return out, (sampler.stop() if sampler else None)
+
+
+def _hbm_peak():
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return peaks.get("hbm_gbs", 6800.0), "measured" if "hbm_gbs" in peaks else "fallback"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_batched(args):
+    """Configuration 4: 512 independent random banded systems (N_k ~ U[2048, 65536], 7-15
+    non-zeros per row, FP32 values), mixed precision, Jacobi, tol 1e-8, one persistent
+    launch replayed from a CUDA graph.  A step is one batch solve of all systems."""
+    import numpy as np
+    import torch
+    import testproblems as tp
+    import paper_1809_01948_gb300 as pb
+    pb.build()
+    dev = torch.device("cuda", 0)
+    c = tp.config4().concat()
+    row_off, nnz_off = c["row_off"], c["nnz_off"]
+    rp = torch.from_numpy(c["row_ptr"]).to(dev)
+    col = torch.from_numpy(c["col"]).to(dev)
+    val = torch.from_numpy(c["val"]).to(dev)
+    b = torch.from_numpy(c["b"]).to(dev)
+    s = pb.BatchSolver(row_off, nnz_off, rp, col, val, precond="jacobi", precision="mixed", tol=1e-8,
+                       max_it=1000, rr_theta=1e-3)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    last = {}
+
+    def one():
+        flush.fill_(1.0)
+        x = torch.zeros_like(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, info = s.solve(b, x)
+        e1.record()
+        torch.cuda.synchronize()
+        last.update(info)
+        return e0.elapsed_time(e1)
+
+    times, clocks = _timed_steps(args, one)
+    ms = statistics.mean(times)
+    sizes = np.diff(row_off)
+    nnz_row = float(nnz_off[-1]) / float(row_off[-1])
+    row_its = float(np.sum(sizes * last["iterations"]))
+    # per row and iteration: 26 FP32 vector streams + FP64 x twice + two CSR reads (FP32 values,
+    # int32 columns, row pointer, D^-1)
+    bpr = 26 * 4 + 2 * 8 + 2 * (nnz_row * 8 + 4 + 4)
+    peak, src = _hbm_peak()
+    ach = bpr * row_its / (last["time_ms"] * 1e-3) / 1e9
+    line = {"metric": "batched p-BiCGStab time to solve all systems to 1e-8", "value": round(ms, 4), "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "batched_512_random_banded_fp32_jacobi_tol1e-8", "n_sys": len(row_off) - 1,
+                       "total_rows": int(row_off[-1]), "nnz_per_row": round(nnz_row, 2),
+                       "launch": "%d x %d, %d block(s) per system (autotuned), CUDA graph" % (
+                           last["grid_blocks"], last["block_threads"], last["cluster_blocks"]),
+                       "l2": "flushed between steps (256 MB write)"},
+            "n_ok": int(last["n_ok"]), "iterations_mean": float(np.mean(last["iterations"])),
+            "iterations_max": int(np.max(last["iterations"])), "kernel_ms": round(last["time_ms"], 4),
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "traffic": None, "peak_source": src,
+                         "bytes_per_row_iteration": round(bpr, 1), "row_iterations": row_its},
+            "e2e": {"value": None, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "clocks": clocks, "gpu_launches": args.steps, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
+def run_autograd(args):
+    """Configuration 5: loss = sum ||X - X_t||^2 with X = A^{-1} B through the differentiable
+    solve (16 right-hand sides on the 512^2 convection-diffusion CSR system, FP64); a step is
+    the forward multi-RHS solve plus the backward pass (transposed-matrix adjoint solve and
+    the value gradient)."""
+    import torch
+    import testproblems as tp
+    import paper_1809_01948_gb300 as pb
+    pb.build()
+    dev = torch.device("cuda", 0)
+    mp = tp.config5()
+    rp = torch.from_numpy(mp.A.row_ptr).to(dev)
+    col = torch.from_numpy(mp.A.col).to(dev)
+    vals0 = torch.from_numpy(mp.A.val).to(dev)
+    B0 = torch.from_numpy(mp.B).to(dev)
+    Xt = torch.from_numpy(mp.X_target).to(dev)
+    opts = dict(precond="jacobi", tol=1e-10, max_it=30000, rr_period=100, rr_theta=1e-3, max_restarts=3)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one():
+        flush.fill_(1.0)
+        vals = vals0.clone().requires_grad_(True)
+        B = B0.clone().requires_grad_(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        X = pb.sparse_solve(vals, B, rp, col, **opts)
+        loss = ((X - Xt) ** 2).sum()
+        loss.backward()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    times, clocks = _timed_steps(args, one)
+    ms = statistics.mean(times)
+    line = {"metric": "differentiable p-BiCGStab: forward + adjoint gradient time", "value": round(ms, 4),
+            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "convdiff2d_512x512_csr_16rhs_autograd_tol1e-10", "n": mp.A.n, "nrhs": mp.B.shape[1],
+                       "l2": "flushed between steps (256 MB write)"},
+            "roofline": None, "e2e": {"value": None, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "clocks": clocks, "gpu_launches": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -429,12 +558,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", action="store_true", help="measure the headline variant only")
     ap.add_argument("--grid", type=int, default=0, help="grid size per dimension (profiling of smaller cases)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
-                    help="c2: 2D convection-diffusion 1024^2 DIA (default); c3: 3D 256^3 CSR Neumann-2")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2: 2D convection-diffusion 1024^2 DIA (default); c3: 3D 256^3 CSR Neumann-2; "
+                         "c4: 512 batched systems; c5: differentiable solve, 16 RHS, forward + backward")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c4":
+        run_batched(args)
+    elif args.workload == "c5":
+        run_autograd(args)
     else:
         run_gpu(args)
 

@@ -130,7 +130,8 @@ typedef struct pbcg_options {
   double rr_tau;           /* tau of Eq. (criterion); <= 0: sqrt(2^-52)               */
   int32_t operator_storage;/* pbcg_storage: PBCG_STORAGE_AUTO (default) or _GENERAL; fixed
                               at create                                                 */
-  int32_t reserved2;
+  int32_t cluster_blocks;  /* batched solver only: thread blocks per system, 1 (one block),
+                              2, 4 or 8 (a thread-block cluster); 0 = autotune          */
 } pbcg_options;
 
 typedef struct pbcg_result {
@@ -251,7 +252,7 @@ typedef struct pbcg_batch_result {
   int32_t n_ok;             /* systems with status PBCG_OK */
   int32_t block_threads;    /* launch shape used (autotuned when the options ask for 0) */
   int32_t grid_blocks;
-  int32_t reserved0;
+  int32_t cluster_blocks;   /* blocks per system (1: one block, else a cluster) */
 } pbcg_batch_result;
 
 typedef struct pbcg_batch_ctx pbcg_batch_ctx;

@@ -238,7 +238,7 @@ class BatchSolver:
 
     def __init__(self, row_off, nnz_off, row_ptr, col, val, precond: str = "jacobi", precision: str = "mixed",
                  tol: float = 1e-8, max_it: int = 1000, rr_period: int = 0, rr_theta: float = 0.0,
-                 grid_blocks: int = 0, block_threads: int = 0, max_restarts: int = 0,
+                 grid_blocks: int = 0, block_threads: int = 0, max_restarts: int = 0, cluster_blocks: int = 0,
                  stream: Optional[torch.cuda.Stream] = None):
         import numpy as np
         lib = _lib()
@@ -263,6 +263,7 @@ class BatchSolver:
         self.opt.rr_period, self.opt.rr_theta = rr_period, rr_theta
         self.opt.grid_blocks, self.opt.block_threads = grid_blocks, block_threads
         self.opt.max_restarts = max_restarts
+        self.opt.cluster_blocks = cluster_blocks
         self.ctx = C.c_void_p()
         _check(lib.pbicgstab_batch_create(C.byref(self.ctx), C.byref(bt), C.byref(self.opt), _stream_handle(stream)),
                "pbicgstab_batch_create")
@@ -283,7 +284,8 @@ class BatchSolver:
         if code in (capi.PBCG_INVALID_ARG, capi.PBCG_CUDA_ERROR, capi.PBCG_OUT_OF_MEMORY, capi.PBCG_TIMEOUT):
             raise PBCGError(code, capi.last_error())
         return x, dict(status=st, iterations=it, n_replacements=nr, rel_res_true=tr, time_ms=res.time_ms,
-                       n_ok=res.n_ok, block_threads=res.block_threads, grid_blocks=res.grid_blocks)
+                       n_ok=res.n_ok, block_threads=res.block_threads, grid_blocks=res.grid_blocks,
+                       cluster_blocks=res.cluster_blocks)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -54,6 +54,46 @@ __device__ __forceinline__ MatView<V> csr_view(int n, const int* rp, const int* 
   return m;
 }
 
+// Parameters of system k for the algorithm body (built by one thread into shared memory).
+template <typename T, typename VR>
+__device__ void build_params(const BatchDev& d, int k, SolverParams<T, VR>& p) {
+  const long long r0 = d.row_off[k], e0 = d.nnz_off[k];
+  const int n = (int)(d.row_off[k + 1] - r0);
+  const int* rp = d.row_ptr + r0 + k;
+  const int* col = d.col + e0;
+  p.n = n;
+  p.chunk = n;
+  p.At = csr_view<T>(n, rp, col, (const T*)d.valAt + e0);
+  p.Au = csr_view<T>(n, rp, col, (const T*)d.valAu + e0);
+  p.A64 = csr_view<VR>(n, rp, col, (const VR*)d.valR + e0);
+  p.dinv = d.dinv ? (const T*)d.dinv + r0 : nullptr;
+  p.dinv_c = T(0);
+  p.prefetch = 0;
+  p.prec = d.prec;
+  p.degree = 0;
+  p.b = d.b + r0;
+  p.x = d.x + r0;
+  T* v = (T*)d.vecs + r0;
+  const size_t R = (size_t)d.total_rows;
+  p.r = v;          p.rh = v + R;      p.k = v + 2 * R;   p.w = v + 3 * R;   p.g = v + 4 * R;
+  p.s = v + 5 * R;  p.l = v + 6 * R;   p.z = v + 7 * R;   p.v = v + 8 * R;   p.t = v + 9 * R;
+  p.nb = v + 10 * R; p.m = v + 11 * R; p.nn = v + 12 * R; p.tmpa = v + 13 * R; p.tmpb = v + 14 * R;
+  p.part = nullptr;
+  p.bar = nullptr;
+  p.err = nullptr;
+  p.res = d.res + k;
+  p.hist_x = nullptr;
+  p.K = 0;
+  p.hist_s = nullptr;
+  p.hist_len = 0;
+  p.tol = d.tol;
+  p.max_it = d.max_it;
+  p.rr_period = d.rr_period;
+  p.rr_theta = d.rr_theta;
+  p.timeout_ns = 0;
+  p.max_restarts = d.max_restarts;
+}
+
 template <typename T, typename VR>
 __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev d) {
   __shared__ double smem[kWork + 3 * kMaxDots];
@@ -69,43 +109,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev 
     const int k = s_sys;
     if (k < 0) return;
     __shared__ SolverParams<T, VR> p;   // per-system parameters, built by thread 0
-    const long long r0 = d.row_off[k], e0 = d.nnz_off[k];
-    const int n = (int)(d.row_off[k + 1] - r0);
-    if (threadIdx.x == 0) {
-      const int* rp = d.row_ptr + r0 + k;
-      const int* col = d.col + e0;
-      p.n = n;
-      p.chunk = n;
-      p.At = csr_view<T>(n, rp, col, (const T*)d.valAt + e0);
-      p.Au = csr_view<T>(n, rp, col, (const T*)d.valAu + e0);
-      p.A64 = csr_view<VR>(n, rp, col, (const VR*)d.valR + e0);
-      p.dinv = d.dinv ? (const T*)d.dinv + r0 : nullptr;
-      p.dinv_c = T(0);
-      p.prefetch = 0;
-      p.prec = d.prec;
-      p.degree = 0;
-      p.b = d.b + r0;
-      p.x = d.x + r0;
-      T* v = (T*)d.vecs + r0;
-      const size_t R = (size_t)d.total_rows;
-      p.r = v;          p.rh = v + R;      p.k = v + 2 * R;   p.w = v + 3 * R;   p.g = v + 4 * R;
-      p.s = v + 5 * R;  p.l = v + 6 * R;   p.z = v + 7 * R;   p.v = v + 8 * R;   p.t = v + 9 * R;
-      p.nb = v + 10 * R; p.m = v + 11 * R; p.nn = v + 12 * R; p.tmpa = v + 13 * R; p.tmpb = v + 14 * R;
-      p.part = nullptr;
-      p.bar = nullptr;
-      p.err = nullptr;
-      p.res = d.res + k;
-      p.hist_x = nullptr;
-      p.K = 0;
-      p.hist_s = nullptr;
-      p.hist_len = 0;
-      p.tol = d.tol;
-      p.max_it = d.max_it;
-      p.rr_period = d.rr_period;
-      p.rr_theta = d.rr_theta;
-      p.timeout_ns = 0;
-      p.max_restarts = d.max_restarts;
-    }
+    const int n = (int)(d.row_off[k + 1] - d.row_off[k]);
+    if (threadIdx.x == 0) build_params(d, k, p);
     __syncthreads();
     BlockTeam team;
     team.first = 0;
@@ -129,6 +134,69 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev 
       p.res->true_rel = bb > 0.0 ? sqrt(rr) / sqrt(bb) : sqrt(rr);
     }
   }
+}
+
+// One thread-block cluster per system: the cluster's blocks share the rows (block rank
+// r takes rows r*blockDim + t, stepping by the cluster's threads), synchronise with the
+// hardware cluster barrier and sum their partials through distributed shared memory.
+// Large systems then run on several SMs while small ones still fill the GPU.  Every block
+// of a cluster takes the same control-flow decisions (the totals are identical), so all
+// reach every cluster barrier.
+template <typename T, typename VR>
+__global__ void __launch_bounds__(kMaxThreads, 1) batched_cluster_kernel(const BatchDev d) {
+  __shared__ double smem[kWork + 5 * kMaxDots];
+  __shared__ double scal[8];
+  __shared__ int s_sys;      // rank 0: the system the cluster works on
+  __shared__ int s_local;    // every block: its copy of it
+  __shared__ SolverParams<T, VR> p;
+  unsigned rank, nrank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(nrank));
+  ClusterTeam team;
+  team.rank = rank;
+  team.nrank = nrank;
+  team.smem = smem;
+  team.scal = scal;
+  for (;;) {
+    team.sync();   // every block is done with the previous system and its s_sys
+    if (rank == 0 && threadIdx.x == 0) {
+      const unsigned q = atomicAdd(d.counter, 1u);
+      s_sys = q < (unsigned)d.n_sys ? d.order[q] : -1;
+    }
+    team.sync();
+    if (threadIdx.x == 0) {
+      const unsigned laddr = (unsigned)__cvta_generic_to_shared(&s_sys);
+      unsigned raddr;
+      int k;
+      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(0u));
+      asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(k) : "r"(raddr) : "memory");
+      s_local = k;
+      if (k >= 0) build_params(d, k, p);
+    }
+    __syncthreads();
+    const int k = s_local;
+    if (k < 0) break;
+    const int n = (int)(d.row_off[k + 1] - d.row_off[k]);
+    team.first = (int)rank * blockDim.x;
+    team.stride = (int)nrank * blockDim.x;
+    team.end = n;
+    solve_body<false>(p, team);
+    team.sync();
+    // final FP64 true residual of this system
+    double a[2] = {0.0, 0.0};
+    for (int i = team.first + threadIdx.x; i < n; i += team.stride) {
+      const double bi = p.b[i];
+      const double r = bi - row_dot<double>(p.A64, p.x, i);
+      a[0] = fma(r, r, a[0]);
+      a[1] = fma(bi, bi, a[1]);
+    }
+    team.template publish<2>(a, 0);
+    team.sync();
+    double t2[2];
+    team.template combine<2>(0, t2);
+    if (team.leader()) p.res->true_rel = t2[1] > 0.0 ? sqrt(t2[0]) / sqrt(t2[1]) : sqrt(t2[0]);
+  }
+  team.sync();   // no block leaves while a peer may still read its shared memory
 }
 
 __global__ void batch_validate_kernel(int n_sys, const long long* row_off, const long long* nnz_off,
@@ -217,8 +285,8 @@ struct pbcg_batch_ctx {
   cudaGraphExec_t exec = nullptr;
   const double* g_b = nullptr;
   double* g_x = nullptr;
-  int g_grid = 0, g_threads = 0;
-  int tuned_grid = 0, tuned_threads = 0;
+  int g_grid = 0, g_threads = 0, g_cluster = 0;
+  int tuned_grid = 0, tuned_threads = 0, tuned_cluster = 0;
 };
 
 static void batch_free(pbcg_batch_ctx* c) {
@@ -237,12 +305,15 @@ static void batch_free(pbcg_batch_ctx* c) {
 }
 
 template <typename T, typename VR>
-static const void* bkernel() { return (const void*)batched_kernel<T, VR>; }
+static const void* bkernel(bool cluster) {
+  return cluster ? (const void*)batched_cluster_kernel<T, VR> : (const void*)batched_kernel<T, VR>;
+}
 
-static const void* pick_kernel(const pbcg_batch_ctx* c) {
+// The one-block-per-system kernel, or (cluster = true) the cluster-per-system kernel.
+static const void* pick_kernel(const pbcg_batch_ctx* c, bool cluster = false) {
   const bool mixed = c->precision == PBCG_MIXED;
-  if (mixed) return c->vr_f32 ? bkernel<float, float>() : bkernel<float, double>();
-  return c->vr_f32 ? bkernel<double, float>() : bkernel<double, double>();
+  if (mixed) return c->vr_f32 ? bkernel<float, float>(cluster) : bkernel<float, double>(cluster);
+  return c->vr_f32 ? bkernel<double, float>(cluster) : bkernel<double, double>(cluster);
 }
 
 static BatchDev make_dev(pbcg_batch_ctx* c, const double* b, double* x) {
@@ -279,29 +350,78 @@ static BatchDev make_dev(pbcg_batch_ctx* c, const double* b, double* x) {
     if (s__ != PBCG_OK) return s__;                      \
   } while (0)
 
-static pbcg_status launch_direct(pbcg_batch_ctx* c, const double* b, double* x, int grid, int threads,
+static void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute& attr, int grid, int threads, int cluster,
+                           cudaStream_t s) {
+  memset(&cfg, 0, sizeof cfg);
+  memset(&attr, 0, sizeof attr);
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = (unsigned)cluster;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+}
+
+static pbcg_status launch_direct(pbcg_batch_ctx* c, const double* b, double* x, int grid, int threads, int cluster,
                                  cudaStream_t s) {
   BCK(cudaMemsetAsync(c->counter, 0, sizeof(unsigned), s), "memset");
   BatchDev d = make_dev(c, b, x);
   void* args[] = {&d};
-  BCK(cudaLaunchKernel(pick_kernel(c), grid, threads, args, 0, s), "batched launch");
+  if (cluster <= 1) {
+    BCK(cudaLaunchKernel(pick_kernel(c), grid, threads, args, 0, s), "batched launch");
+  } else {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr;
+    cluster_config(cfg, attr, grid, threads, cluster, s);
+    BCK(cudaLaunchKernelExC(&cfg, pick_kernel(c, true), args), "batched cluster launch");
+  }
   return PBCG_OK;
 }
 
-static pbcg_status candidate_shapes(const pbcg_batch_ctx* c, std::vector<std::pair<int, int>>& out) {
+struct BatchShape {
+  int grid, threads, cluster;
+};
+
+// Clusters of `cluster` blocks that can be resident at once for this block size (0: none).
+static pbcg_status active_clusters(const pbcg_batch_ctx* c, int threads, int cluster, int* n) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr;
+  cluster_config(cfg, attr, cluster, threads, cluster, c->stream);
+  *n = 0;
+  BCK(cudaOccupancyMaxActiveClusters(n, pick_kernel(c, true), &cfg), "cluster occupancy");
+  return PBCG_OK;
+}
+
+// Candidate launch shapes: one block per system at 256/512/1024 threads and 1-4 blocks per
+// SM, and clusters of 2, 4 or 8 blocks per system at every resident cluster count.
+static pbcg_status candidate_shapes(const pbcg_batch_ctx* c, std::vector<BatchShape>& out, int only_cluster) {
   const int sms = sm_count();
   const int tlist[] = {256, 512, 1024};
   for (int t : tlist) {
-    int per = 0;
-    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pick_kernel(c), t, 0), "occupancy");
-    for (int bps = 1; bps <= std::min(per, 4); ++bps) out.push_back({sms * bps, t});
+    if (only_cluster <= 1) {
+      int per = 0;
+      BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pick_kernel(c), t, 0), "occupancy");
+      for (int bps = 1; bps <= std::min(per, 4); ++bps) out.push_back({sms * bps, t, 1});
+    }
+    for (int cl = 2; cl <= 8; cl *= 2) {
+      if (only_cluster > 1 && cl != only_cluster) continue;
+      if (only_cluster == 1) continue;
+      int nc = 0;
+      pbcg_status st = active_clusters(c, t, cl, &nc);
+      if (st != PBCG_OK) return st;
+      if (nc > 0) out.push_back({nc * cl, t, cl});
+    }
   }
   return PBCG_OK;
 }
 
 static pbcg_status autotune(pbcg_batch_ctx* c, const double* b, double* x) {
-  std::vector<std::pair<int, int>> cands;
-  pbcg_status st = candidate_shapes(c, cands);
+  std::vector<BatchShape> cands;
+  pbcg_status st = candidate_shapes(c, cands, c->opt.cluster_blocks);
   if (st != PBCG_OK) return st;
   double* xs = nullptr;
   BCK(cudaMallocAsync((void**)&xs, sizeof(double) * c->total_rows, c->stream), "autotune scratch");
@@ -309,13 +429,13 @@ static pbcg_status autotune(pbcg_batch_ctx* c, const double* b, double* x) {
   for (auto& sh : cands) {
     cudaMemcpyAsync(xs, x, sizeof(double) * c->total_rows, cudaMemcpyDeviceToDevice, c->stream);
     cudaEventRecord(c->ev0, c->stream);
-    st = launch_direct(c, b, xs, sh.first, sh.second, c->stream);
+    st = launch_direct(c, b, xs, sh.grid, sh.threads, sh.cluster, c->stream);
     if (st != PBCG_OK) break;
     cudaEventRecord(c->ev1, c->stream);
     if (cudaEventSynchronize(c->ev1) != cudaSuccess) { st = cuda_status(cudaGetLastError(), "autotune"); break; }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    if (ms < best) { best = ms; c->tuned_grid = sh.first; c->tuned_threads = sh.second; }
+    if (ms < best) { best = ms; c->tuned_grid = sh.grid; c->tuned_threads = sh.threads; c->tuned_cluster = sh.cluster; }
   }
   cudaFreeAsync(xs, c->stream);
   return st;
@@ -338,6 +458,9 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
   if (opt->block_threads != 0 && (opt->block_threads < 32 || opt->block_threads > kMaxThreads || opt->block_threads % 32))
     return set_error(PBCG_INVALID_ARG, "block_threads must be 0 or a multiple of 32 in [32, 1024]");
   if (opt->max_restarts < 0 || opt->max_restarts > 1000) return set_error(PBCG_INVALID_ARG, "max_restarts must be in [0, 1000]");
+  if (opt->cluster_blocks != 0 && opt->cluster_blocks != 1 && opt->cluster_blocks != 2 && opt->cluster_blocks != 4 &&
+      opt->cluster_blocks != 8)
+    return set_error(PBCG_INVALID_ARG, "cluster_blocks must be 0, 1, 2, 4 or 8");
   const int ns = B->n_sys;
   if (B->row_off[0] != 0 || B->nnz_off[0] != 0) return set_error(PBCG_INVALID_ARG, "offsets must start at 0");
   for (int k = 0; k < ns; ++k) {
@@ -440,12 +563,13 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
 #undef CKB
 }
 
-static pbcg_status ensure_graph(pbcg_batch_ctx* c, const double* b, double* x, int grid, int threads) {
-  if (c->exec && c->g_b == b && c->g_x == x && c->g_grid == grid && c->g_threads == threads) return PBCG_OK;
+static pbcg_status ensure_graph(pbcg_batch_ctx* c, const double* b, double* x, int grid, int threads, int cluster) {
+  if (c->exec && c->g_b == b && c->g_x == x && c->g_grid == grid && c->g_threads == threads && c->g_cluster == cluster)
+    return PBCG_OK;
   if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
   cudaGraph_t graph = nullptr;
   BCK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-  pbcg_status st = launch_direct(c, b, x, grid, threads, c->cap_stream);
+  pbcg_status st = launch_direct(c, b, x, grid, threads, cluster, c->cap_stream);
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
   if (st != PBCG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
   BCK(e, "end capture");
@@ -456,12 +580,13 @@ static pbcg_status ensure_graph(pbcg_batch_ctx* c, const double* b, double* x, i
   c->g_x = x;
   c->g_grid = grid;
   c->g_threads = threads;
+  c->g_cluster = cluster;
   return PBCG_OK;
 }
 
 extern "C" pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* c, const double* b, double* x, pbcg_batch_result* res) {
   if (!c || !b || !x) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_batch_solve");
-  int grid = c->opt.grid_blocks, threads = c->opt.block_threads;
+  int grid = c->opt.grid_blocks, threads = c->opt.block_threads, cluster = std::max(1, c->opt.cluster_blocks);
   if (grid == 0 || threads == 0) {
     if (!c->tuned_grid) {
       pbcg_status st = autotune(c, b, x);
@@ -469,8 +594,15 @@ extern "C" pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* c, const double* b,
     }
     grid = c->tuned_grid;
     threads = c->tuned_threads;
+    cluster = c->tuned_cluster;
+  } else if (cluster > 1) {
+    int nc = 0;
+    pbcg_status st = active_clusters(c, threads, cluster, &nc);
+    if (st != PBCG_OK) return st;
+    if (grid % cluster || grid / cluster > nc)
+      return set_error(PBCG_INVALID_ARG, "grid_blocks must be a multiple of the cluster size and fit on the GPU");
   }
-  pbcg_status st = ensure_graph(c, b, x, grid, threads);
+  pbcg_status st = ensure_graph(c, b, x, grid, threads, cluster);
   if (st != PBCG_OK) return st;
   BCK(cudaEventRecord(c->ev0, c->stream), "event");
   BCK(cudaGraphLaunch(c->exec, c->stream), "graph launch");
@@ -483,6 +615,7 @@ extern "C" pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* c, const double* b,
   res->time_ms = ms;
   res->block_threads = threads;
   res->grid_blocks = grid;
+  res->cluster_blocks = cluster;
   int nok = 0;
   pbcg_status first_bad = PBCG_OK;
   for (int k = 0; k < c->n_sys; ++k) {

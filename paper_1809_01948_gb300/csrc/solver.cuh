@@ -219,6 +219,48 @@ struct BlockTeam {
   __device__ __forceinline__ bool leader() const { return threadIdx.x == 0; }
 };
 
+// A thread-block cluster solves one system (batched solver): rows are dealt to the
+// cluster's blocks in turn, sync() is the hardware cluster barrier, and each block's
+// partials stay in its own shared memory, from which every block sums all ranks' values
+// in rank order through distributed shared memory -- identical totals in every block.
+struct ClusterTeam {
+  int first, stride, end;
+  unsigned rank, nrank;
+  double* smem;   // >= kWork + 5*kMaxDots doubles
+  double* scal;   // >= 8 doubles
+  __device__ __forceinline__ bool sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    return true;
+  }
+  template <int ND>
+  __device__ __forceinline__ void publish(double (&v)[ND], int set) {
+    block_reduce<ND>(v, smem, smem + kWork + set * kMaxDots);
+  }
+  // Valid after the sync() that follows every rank's publish of `set`; a rank publishes
+  // the same set again only after a later sync(), so the reads below never race with it.
+  template <int ND>
+  __device__ __forceinline__ void combine(int set, double (&out)[ND]) {
+    double* tot = smem + kWork + 4 * kMaxDots;   // this block's copy of the totals
+    if (threadIdx.x < ND) {
+      const unsigned laddr = (unsigned)__cvta_generic_to_shared(smem + kWork + set * kMaxDots + threadIdx.x);
+      double acc = 0.0;
+      for (unsigned q = 0; q < nrank; ++q) {   // rank order: the same sum in every block
+        unsigned raddr;
+        double v;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(q));
+        asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(raddr) : "memory");
+        acc += v;
+      }
+      tot[threadIdx.x] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int d = 0; d < ND; ++d) out[d] = tot[d];
+    __syncthreads();
+  }
+  __device__ __forceinline__ bool leader() const { return rank == 0 && threadIdx.x == 0; }
+};
+
 // d_inv of row i: the stored vector, or the one value of a constant diagonal.
 template <typename T, typename VR>
 __device__ __forceinline__ T dinv_at(const SolverParams<T, VR>& p, int i) {

@@ -79,3 +79,55 @@ def test_batched_invalid_input_rejected():
     with pytest.raises(pb.PBCGError) as e:
         pb.BatchSolver(row_off, nnz_off, rp, col, val)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+def test_batched_cluster_per_system_matches_single_solver(cluster):
+    """A thread-block cluster per system (rows dealt to the cluster's blocks, cluster barrier,
+    partials summed through distributed shared memory) solves every system as the
+    single-system solver does; sizes include systems smaller than one block's threads."""
+    torch = torch_cuda()
+    from gpu_common import make_solver, gpu_solve
+    import paper_1809_01948_gb300 as pb
+    bp = tp.config4(nsys=12, n_lo=20, n_hi=6000, band=64)
+    c = bp.concat()
+    dev = torch.device("cuda:0")
+    s = pb.BatchSolver(c["row_off"], c["nnz_off"], torch.from_numpy(c["row_ptr"]).to(dev),
+                       torch.from_numpy(c["col"]).to(dev), torch.from_numpy(c["val"]).to(dev), precision="fp64",
+                       tol=1e-12, max_it=800, rr_period=50, grid_blocks=4 * cluster, block_threads=256,
+                       cluster_blocks=cluster)
+    b = torch.from_numpy(c["b"]).to(dev)
+    x, info = s.solve(b)
+    assert info["cluster_blocks"] == cluster and info["grid_blocks"] == 4 * cluster
+    x = x.cpu().numpy()
+    assert info["n_ok"] == 12, info["status"]
+    for k, sysk in enumerate(bp.systems):
+        xk = x[c["row_off"][k]:c["row_off"][k + 1]]
+        true = np.linalg.norm(sysk.b - sysk.A.to_scipy(np.float64) @ xk) / np.linalg.norm(sysk.b)
+        assert true <= 1e-11 and abs(true - info["rel_res_true"][k]) <= 1e-3 * true + 1e-18
+        single = make_solver(tp.Problem("s", sysk.A, sysk.b, sysk.x0, None, precond="jacobi", fmt="csr"),
+                             tol=1e-12, max_it=800, rr_period=50)
+        xs, res, _, _ = gpu_solve(single, sysk.b)
+        assert res.status == 0
+        assert np.linalg.norm(xk - xs) <= 1e-10 * np.linalg.norm(xs)
+    # replay from the captured graph: bitwise identical
+    x2, info2 = s.solve(b, torch.zeros_like(b))
+    assert np.array_equal(x, x2.cpu().numpy()) and np.array_equal(info["iterations"], info2["iterations"])
+
+
+def test_batched_cluster_mixed_and_autotune_choice():
+    bp = tp.config4(nsys=30, n_lo=1000, n_hi=20000, band=128)
+    s, c, b = _batch_solver(bp, precision="mixed", tol=1e-8, max_it=500, rr_theta=1e-3, cluster_blocks=4)
+    x, info = s.solve(b)
+    assert info["n_ok"] == 30 and info["cluster_blocks"] == 4
+    s2, _, _ = _batch_solver(bp, precision="mixed", tol=1e-8, max_it=500, rr_theta=1e-3)
+    x2, info2 = s2.solve(b)   # autotune over one-block and cluster shapes
+    assert info2["n_ok"] == 30 and info2["cluster_blocks"] in (1, 2, 4, 8)
+
+
+def test_batched_cluster_option_rejected():
+    torch = torch_cuda()
+    import paper_1809_01948_gb300 as pb
+    bp = tp.config4(nsys=3, n_lo=100, n_hi=200, band=16)
+    with pytest.raises(pb.PBCGError):
+        _batch_solver(bp, cluster_blocks=3)
