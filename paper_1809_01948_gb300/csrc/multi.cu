@@ -117,8 +117,11 @@ template <typename T>
 static pbcg_status launch_wave(pbcg_ctx* c, int teams, int bpt, int nt, const double* B, double* X) {
   SolverParams<T>* hp = (SolverParams<T>*)c->multi_hparams;
   const size_t n = (size_t)c->n;
+  // the teams stream their own vectors side by side: prefetch when together they exceed L2
+  const int prefetch = (c->stencil && teams * hot_bytes(c) > (double)l2_bytes()) ? 1 : 0;
   for (int t = 0; t < teams; ++t) {
     SolverParams<T> p = make_params<T>(c, B + t * n, X + t * n, bpt);
+    p.prefetch = prefetch;
     T* v = (T*)c->multi_vecs + (size_t)t * 15 * n;
     T** slots[] = {&p.r, &p.rh, &p.k, &p.w, &p.g, &p.s, &p.l, &p.z, &p.v, &p.t, &p.nb, &p.m, &p.nn, &p.tmpa, &p.tmpb};
     for (int j = 0; j < 15; ++j) *slots[j] = v + (size_t)j * n;
