@@ -206,6 +206,8 @@ def run_gpu(args):
         # Algorithm 1, the paper's reference method, on the same system (three reduction
         # phases per iteration instead of two)
         variants["classic"] = dict(precision="fp64", method="classic", rr_period=0, rr_theta=0.0)
+        # the relative replacement trigger instead of the period (fewer replacements)
+        variants["fp64_theta"] = dict(precision="fp64", rr_period=0, rr_theta=1e-3)
     # the headline variant with the matrix values kept as given (CSR / DIA) instead of the
     # constant-coefficient stencil storage the library selects for these operators
     variants[args.precision + "_general"] = dict(variants[args.precision], operator_storage="general")
