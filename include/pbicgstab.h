@@ -117,8 +117,9 @@ typedef struct pbcg_options {
   double* hist_x;          /* device, K*n doubles, or NULL when K == 0                */
   double* hist_scalars;    /* device, hist_len*PBCG_HIST_STRIDE doubles, or NULL      */
   int32_t grid_blocks;     /* persistent grid size; 0 = automatic                     */
-  int32_t block_threads;   /* threads per block, a multiple of 32 up to 1024 (FP64) or
-                              512 (mixed; INVALID_ARG above); 0 = that maximum          */
+  int32_t block_threads;   /* threads per block, a multiple of 32 up to 1024, or up to
+                              512 for a mixed solve whose working set exceeds L2
+                              (INVALID_ARG above); 0 = that maximum                     */
   int32_t max_restarts;    /* after a breakdown (zero or non-finite omega, (r0,r_i),
                               beta or alpha denominator) restart Algorithm 2 from the
                               current iterate with a new shadow vector, at most this many

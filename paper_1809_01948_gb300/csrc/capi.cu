@@ -314,27 +314,37 @@ static pbcg_status check_method_precond(const pbcg_options* o, int prec_kind) {
   return PBCG_OK;
 }
 
+// The mixed solver streams from DRAM (STREAM build, 512-thread blocks) when its working set
+// exceeds L2; everything else uses the 1024-thread build.
+static bool streaming(const pbcg_ctx* c) {
+  return c->precision == PBCG_MIXED && !c->opt.rr_auto && c->opt.method == PBCG_PIPELINED &&
+         hot_bytes(c) > (double)l2_bytes();
+}
+
 template <typename T>
-static const void* kernel_ptr(const pbcg_options& o) {
+static const void* kernel_ptr(const pbcg_ctx* c) {
+  const pbcg_options& o = c->opt;
   if constexpr (std::is_same<T, double>::value) {
     if (o.method == PBCG_CLASSIC) return (const void*)classic_kernel<double>;
+  } else {
+    if (streaming(c)) return (const void*)pbicgstab_kernel<float, false, true>;
   }
   return o.rr_auto ? (const void*)pbicgstab_kernel<T, true> : (const void*)pbicgstab_kernel<T, false>;
 }
 
-// Default shape: the solver kernels' register budgets (SolverLaunch): FP64 one 1024-thread
-// block per SM (measured faster than two 512-thread blocks on the 2D and 3D
-// convection-diffusion systems: fewer blocks at each grid barrier and reduction), mixed
-// three 512-thread blocks per SM.
+// Default shape: the solver kernels' register budgets (SolverLaunch): one 1024-thread block
+// per SM (measured faster than two 512-thread blocks on the 2D and 3D convection-diffusion
+// systems: fewer blocks at each grid barrier and reduction), three 512-thread blocks per
+// SM for the streaming mixed build.
 static int kernel_threads(const pbcg_ctx* c) {
   if (c->opt.block_threads) return c->opt.block_threads;
-  return c->precision == PBCG_MIXED ? pbcg::SolverLaunch<float>::kThreads : pbcg::SolverLaunch<double>::kThreads;
+  return streaming(c) ? pbcg::SolverLaunch<float, true>::kThreads : pbcg::SolverLaunch<double, false>::kThreads;
 }
 
 pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads) {
   const int nt = kernel_threads(c);
   int per_sm = 0;
-  const void* k = c->precision == PBCG_MIXED ? kernel_ptr<float>(c->opt) : kernel_ptr<double>(c->opt);
+  const void* k = c->precision == PBCG_MIXED ? kernel_ptr<float>(c) : kernel_ptr<double>(c);
   cudaFuncAttributes fa;
   CK(cudaFuncGetAttributes(&fa, k), "kernel attributes");
   if (nt > fa.maxThreadsPerBlock)
@@ -591,11 +601,11 @@ static pbcg_status enqueue_solve(pbcg_ctx* c, const double* b, double* x) {
   if (c->precision == PBCG_MIXED) {
     SolverParams<float> p = make_params<float>(c, b, x, grid);
     void* args[] = {&p};
-    CK(cudaLaunchCooperativeKernel(kernel_ptr<float>(c->opt), grid, threads, args, 0, c->stream), "cooperative launch");
+    CK(cudaLaunchCooperativeKernel(kernel_ptr<float>(c), grid, threads, args, 0, c->stream), "cooperative launch");
   } else {
     SolverParams<double> p = make_params<double>(c, b, x, grid);
     void* args[] = {&p};
-    CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(c->opt), grid, threads, args, 0, c->stream), "cooperative launch");
+    CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(c), grid, threads, args, 0, c->stream), "cooperative launch");
   }
   CK(cudaEventRecord(c->ev1, c->stream), "event record");
   return enqueue_true_residual(c, b, x, &c->dstate->true_rel);

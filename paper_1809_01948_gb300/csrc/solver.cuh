@@ -738,22 +738,23 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
 #undef PBCG_BCAST_DONE
 }
 
-// Register budget of the persistent solver per precision.  FP64 is bound by the FP64
-// pipe and keeps 64 registers (one 1024-thread block per SM); the FP32 recurrences of the
-// mixed solver are bound by memory-level parallelism where the working set exceeds L2, so
-// they trade registers (40, with some spilling) for 48 resident warps per SM (three
-// 512-thread blocks): 1173 vs 1301 us per iteration on the 256^3 Neumann system, while
-// FP64 at that budget loses 12%.
-template <typename T>
+// Register budget of the persistent solver.  FP64 is bound by the FP64 pipe and keeps 64
+// registers (one 1024-thread block per SM).  The FP32 recurrences of the mixed solver come
+// in two builds: where the working set stays in L2 the same 64-register shape is fastest
+// (2D mixed: 46 vs 64 us per iteration), where it streams from DRAM the iteration is bound
+// by memory-level parallelism, so STREAM trades registers (40, with some spilling) for 48
+// resident warps per SM (three 512-thread blocks): 1173 vs 1301 us per iteration on the
+// 256^3 Neumann system (FP64 at that budget loses 12%).
+template <typename T, bool STREAM>
 struct SolverLaunch {
-  static constexpr int kThreads = sizeof(T) == 4 ? 512 : kMaxThreads;
-  static constexpr int kBlocksPerSM = sizeof(T) == 4 ? 3 : 1;
+  static constexpr int kThreads = STREAM ? 512 : kMaxThreads;
+  static constexpr int kBlocksPerSM = STREAM ? 3 : 1;
 };
 
 // One cooperative grid solves one system.  AUTO adds the automated replacement policy
 // (extra norms in the reductions and the gap bound in thread 0).
-template <typename T, bool AUTO>
-__global__ void __launch_bounds__(SolverLaunch<T>::kThreads, SolverLaunch<T>::kBlocksPerSM)
+template <typename T, bool AUTO, bool STREAM = false>
+__global__ void __launch_bounds__(SolverLaunch<T, STREAM>::kThreads, SolverLaunch<T, STREAM>::kBlocksPerSM)
     pbicgstab_kernel(const SolverParams<T> p) {
   __shared__ double smem[kWork + 3 * kMaxDots];
   __shared__ double scal[8];
