@@ -133,6 +133,9 @@ typedef struct pbcg_options {
                               at create                                                 */
   int32_t cluster_blocks;  /* batched solver only: thread blocks per system, 1 (one block),
                               2, 4 or 8 (a thread-block cluster); 0 = autotune          */
+  int32_t lanes_per_row;   /* batched solver only: threads per matrix row in the SpMVs of
+                              the two passes, 1, 2, 4 or 8; 0 = autotune                 */
+  int32_t reserved3;
 } pbcg_options;
 
 typedef struct pbcg_result {
@@ -254,6 +257,8 @@ typedef struct pbcg_batch_result {
   int32_t block_threads;    /* launch shape used (autotuned when the options ask for 0) */
   int32_t grid_blocks;
   int32_t cluster_blocks;   /* blocks per system (1: one block, else a cluster) */
+  int32_t lanes_per_row;    /* threads per row in the SpMVs */
+  int32_t reserved1;
 } pbcg_batch_result;
 
 typedef struct pbcg_batch_ctx pbcg_batch_ctx;

@@ -239,7 +239,7 @@ class BatchSolver:
     def __init__(self, row_off, nnz_off, row_ptr, col, val, precond: str = "jacobi", precision: str = "mixed",
                  tol: float = 1e-8, max_it: int = 1000, rr_period: int = 0, rr_theta: float = 0.0,
                  grid_blocks: int = 0, block_threads: int = 0, max_restarts: int = 0, cluster_blocks: int = 0,
-                 stream: Optional[torch.cuda.Stream] = None):
+                 lanes_per_row: int = 0, stream: Optional[torch.cuda.Stream] = None):
         import numpy as np
         lib = _lib()
         self.row_off = np.ascontiguousarray(row_off, dtype=np.int64)
@@ -264,6 +264,7 @@ class BatchSolver:
         self.opt.grid_blocks, self.opt.block_threads = grid_blocks, block_threads
         self.opt.max_restarts = max_restarts
         self.opt.cluster_blocks = cluster_blocks
+        self.opt.lanes_per_row = lanes_per_row
         self.ctx = C.c_void_p()
         _check(lib.pbicgstab_batch_create(C.byref(self.ctx), C.byref(bt), C.byref(self.opt), _stream_handle(stream)),
                "pbicgstab_batch_create")
@@ -285,7 +286,7 @@ class BatchSolver:
             raise PBCGError(code, capi.last_error())
         return x, dict(status=st, iterations=it, n_replacements=nr, rel_res_true=tr, time_ms=res.time_ms,
                        n_ok=res.n_ok, block_threads=res.block_threads, grid_blocks=res.grid_blocks,
-                       cluster_blocks=res.cluster_blocks)
+                       cluster_blocks=res.cluster_blocks, lanes_per_row=res.lanes_per_row)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -39,6 +39,7 @@ struct BatchDev {
   int rr_period;
   double rr_theta;
   int max_restarts;
+  int lanes;                  // threads per row in the SpMVs of passes A and B
 };
 
 template <typename V>
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev 
     team.first = 0;
     team.stride = blockDim.x;
     team.end = n;
+    team.lanes = d.lanes;
     team.smem = smem;
     team.scal = scal;
     solve_body<false>(p, team);
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_cluster_kernel(const B
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(nrank));
   ClusterTeam team;
+  team.lanes = d.lanes;
   team.rank = rank;
   team.nrank = nrank;
   team.smem = smem;
@@ -285,8 +288,8 @@ struct pbcg_batch_ctx {
   cudaGraphExec_t exec = nullptr;
   const double* g_b = nullptr;
   double* g_x = nullptr;
-  int g_grid = 0, g_threads = 0, g_cluster = 0;
-  int tuned_grid = 0, tuned_threads = 0, tuned_cluster = 0;
+  int g_grid = 0, g_threads = 0, g_cluster = 0, g_lanes = 0;
+  int tuned_grid = 0, tuned_threads = 0, tuned_cluster = 0, tuned_lanes = 0;
 };
 
 static void batch_free(pbcg_batch_ctx* c) {
@@ -316,7 +319,7 @@ static const void* pick_kernel(const pbcg_batch_ctx* c, bool cluster = false) {
   return c->vr_f32 ? bkernel<double, float>(cluster) : bkernel<double, double>(cluster);
 }
 
-static BatchDev make_dev(pbcg_batch_ctx* c, const double* b, double* x) {
+static BatchDev make_dev(pbcg_batch_ctx* c, const double* b, double* x, int lanes) {
   BatchDev d;
   memset(&d, 0, sizeof d);
   d.n_sys = c->n_sys;
@@ -341,6 +344,7 @@ static BatchDev make_dev(pbcg_batch_ctx* c, const double* b, double* x) {
   d.rr_period = c->opt.rr_period;
   d.rr_theta = c->opt.rr_theta;
   d.max_restarts = c->opt.max_restarts;
+  d.lanes = lanes;
   return d;
 }
 
@@ -367,9 +371,9 @@ static void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute& attr, i
 }
 
 static pbcg_status launch_direct(pbcg_batch_ctx* c, const double* b, double* x, int grid, int threads, int cluster,
-                                 cudaStream_t s) {
+                                 int lanes, cudaStream_t s) {
   BCK(cudaMemsetAsync(c->counter, 0, sizeof(unsigned), s), "memset");
-  BatchDev d = make_dev(c, b, x);
+  BatchDev d = make_dev(c, b, x, lanes);
   void* args[] = {&d};
   if (cluster <= 1) {
     BCK(cudaLaunchKernel(pick_kernel(c), grid, threads, args, 0, s), "batched launch");
@@ -383,7 +387,7 @@ static pbcg_status launch_direct(pbcg_batch_ctx* c, const double* b, double* x, 
 }
 
 struct BatchShape {
-  int grid, threads, cluster;
+  int grid, threads, cluster, lanes;
 };
 
 // Clusters of `cluster` blocks that can be resident at once for this block size (0: none).
@@ -405,7 +409,7 @@ static pbcg_status candidate_shapes(const pbcg_batch_ctx* c, std::vector<BatchSh
     if (only_cluster <= 1) {
       int per = 0;
       BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pick_kernel(c), t, 0), "occupancy");
-      for (int bps = 1; bps <= std::min(per, 4); ++bps) out.push_back({sms * bps, t, 1});
+      for (int bps = 1; bps <= std::min(per, 4); ++bps) out.push_back({sms * bps, t, 1, 1});
     }
     for (int cl = 2; cl <= 8; cl *= 2) {
       if (only_cluster > 1 && cl != only_cluster) continue;
@@ -413,12 +417,15 @@ static pbcg_status candidate_shapes(const pbcg_batch_ctx* c, std::vector<BatchSh
       int nc = 0;
       pbcg_status st = active_clusters(c, t, cl, &nc);
       if (st != PBCG_OK) return st;
-      if (nc > 0) out.push_back({nc * cl, t, cl});
+      if (nc > 0) out.push_back({nc * cl, t, cl, 1});
     }
   }
   return PBCG_OK;
 }
 
+// Times one batch solve per candidate on a scratch copy of x: first the launch shapes with
+// one thread per row, then 2, 4 and 8 threads per row in the SpMVs on the best shape
+// (options.lanes_per_row fixes that choice).
 static pbcg_status autotune(pbcg_batch_ctx* c, const double* b, double* x) {
   std::vector<BatchShape> cands;
   pbcg_status st = candidate_shapes(c, cands, c->opt.cluster_blocks);
@@ -426,16 +433,34 @@ static pbcg_status autotune(pbcg_batch_ctx* c, const double* b, double* x) {
   double* xs = nullptr;
   BCK(cudaMallocAsync((void**)&xs, sizeof(double) * c->total_rows, c->stream), "autotune scratch");
   float best = 1e30f;
-  for (auto& sh : cands) {
+  auto trial = [&](const BatchShape& sh) -> pbcg_status {
     cudaMemcpyAsync(xs, x, sizeof(double) * c->total_rows, cudaMemcpyDeviceToDevice, c->stream);
     cudaEventRecord(c->ev0, c->stream);
-    st = launch_direct(c, b, xs, sh.grid, sh.threads, sh.cluster, c->stream);
-    if (st != PBCG_OK) break;
+    pbcg_status s2 = launch_direct(c, b, xs, sh.grid, sh.threads, sh.cluster, sh.lanes, c->stream);
+    if (s2 != PBCG_OK) return s2;
     cudaEventRecord(c->ev1, c->stream);
-    if (cudaEventSynchronize(c->ev1) != cudaSuccess) { st = cuda_status(cudaGetLastError(), "autotune"); break; }
+    if (cudaEventSynchronize(c->ev1) != cudaSuccess) return cuda_status(cudaGetLastError(), "autotune");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    if (ms < best) { best = ms; c->tuned_grid = sh.grid; c->tuned_threads = sh.threads; c->tuned_cluster = sh.cluster; }
+    if (ms < best) {
+      best = ms;
+      c->tuned_grid = sh.grid; c->tuned_threads = sh.threads; c->tuned_cluster = sh.cluster; c->tuned_lanes = sh.lanes;
+    }
+    return PBCG_OK;
+  };
+  const int fixed_lanes = c->opt.lanes_per_row;
+  for (auto& sh : cands) {
+    BatchShape s1 = sh;
+    s1.lanes = fixed_lanes ? fixed_lanes : 1;
+    if ((st = trial(s1)) != PBCG_OK) break;
+  }
+  if (st == PBCG_OK && !fixed_lanes) {
+    const BatchShape base{c->tuned_grid, c->tuned_threads, c->tuned_cluster, 1};
+    for (int L = 2; L <= 8 && st == PBCG_OK; L *= 2) {
+      BatchShape s2 = base;
+      s2.lanes = L;
+      st = trial(s2);
+    }
   }
   cudaFreeAsync(xs, c->stream);
   return st;
@@ -461,6 +486,9 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
   if (opt->cluster_blocks != 0 && opt->cluster_blocks != 1 && opt->cluster_blocks != 2 && opt->cluster_blocks != 4 &&
       opt->cluster_blocks != 8)
     return set_error(PBCG_INVALID_ARG, "cluster_blocks must be 0, 1, 2, 4 or 8");
+  if (opt->lanes_per_row != 0 && opt->lanes_per_row != 1 && opt->lanes_per_row != 2 && opt->lanes_per_row != 4 &&
+      opt->lanes_per_row != 8)
+    return set_error(PBCG_INVALID_ARG, "lanes_per_row must be 0, 1, 2, 4 or 8");
   const int ns = B->n_sys;
   if (B->row_off[0] != 0 || B->nnz_off[0] != 0) return set_error(PBCG_INVALID_ARG, "offsets must start at 0");
   for (int k = 0; k < ns; ++k) {
@@ -563,13 +591,15 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
 #undef CKB
 }
 
-static pbcg_status ensure_graph(pbcg_batch_ctx* c, const double* b, double* x, int grid, int threads, int cluster) {
-  if (c->exec && c->g_b == b && c->g_x == x && c->g_grid == grid && c->g_threads == threads && c->g_cluster == cluster)
+static pbcg_status ensure_graph(pbcg_batch_ctx* c, const double* b, double* x, int grid, int threads, int cluster,
+                                int lanes) {
+  if (c->exec && c->g_b == b && c->g_x == x && c->g_grid == grid && c->g_threads == threads && c->g_cluster == cluster &&
+      c->g_lanes == lanes)
     return PBCG_OK;
   if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
   cudaGraph_t graph = nullptr;
   BCK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-  pbcg_status st = launch_direct(c, b, x, grid, threads, cluster, c->cap_stream);
+  pbcg_status st = launch_direct(c, b, x, grid, threads, cluster, lanes, c->cap_stream);
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
   if (st != PBCG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
   BCK(e, "end capture");
@@ -581,12 +611,14 @@ static pbcg_status ensure_graph(pbcg_batch_ctx* c, const double* b, double* x, i
   c->g_grid = grid;
   c->g_threads = threads;
   c->g_cluster = cluster;
+  c->g_lanes = lanes;
   return PBCG_OK;
 }
 
 extern "C" pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* c, const double* b, double* x, pbcg_batch_result* res) {
   if (!c || !b || !x) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_batch_solve");
   int grid = c->opt.grid_blocks, threads = c->opt.block_threads, cluster = std::max(1, c->opt.cluster_blocks);
+  int lanes = std::max(1, c->opt.lanes_per_row);
   if (grid == 0 || threads == 0) {
     if (!c->tuned_grid) {
       pbcg_status st = autotune(c, b, x);
@@ -595,6 +627,7 @@ extern "C" pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* c, const double* b,
     grid = c->tuned_grid;
     threads = c->tuned_threads;
     cluster = c->tuned_cluster;
+    lanes = c->tuned_lanes;
   } else if (cluster > 1) {
     int nc = 0;
     pbcg_status st = active_clusters(c, threads, cluster, &nc);
@@ -602,7 +635,7 @@ extern "C" pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* c, const double* b,
     if (grid % cluster || grid / cluster > nc)
       return set_error(PBCG_INVALID_ARG, "grid_blocks must be a multiple of the cluster size and fit on the GPU");
   }
-  pbcg_status st = ensure_graph(c, b, x, grid, threads, cluster);
+  pbcg_status st = ensure_graph(c, b, x, grid, threads, cluster, lanes);
   if (st != PBCG_OK) return st;
   BCK(cudaEventRecord(c->ev0, c->stream), "event");
   BCK(cudaGraphLaunch(c->exec, c->stream), "graph launch");
@@ -616,6 +649,7 @@ extern "C" pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* c, const double* b,
   res->block_threads = threads;
   res->grid_blocks = grid;
   res->cluster_blocks = cluster;
+  res->lanes_per_row = lanes;
   int nok = 0;
   pbcg_status first_bad = PBCG_OK;
   for (int k = 0; k < c->n_sys; ++k) {

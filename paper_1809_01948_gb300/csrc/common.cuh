@@ -68,6 +68,22 @@ __device__ __forceinline__ Acc row_dot(const MatView<V>& A, const X* __restrict_
   return acc;
 }
 
+// CSR row product split over the L lanes of a lane group (L a power of two <= 32, the
+// group's lanes consecutive in a warp and all active): lane `sub` takes entries sub,
+// sub + L, ...; the partial sums are combined by shuffles, and every lane of the group
+// returns the total.  Shortens the chain of dependent column -> x loads per thread.
+template <typename Acc, typename V, typename X>
+__device__ __forceinline__ Acc row_dot_lanes(const MatView<V>& A, const X* __restrict__ x, int i, int sub, int L) {
+  Acc acc = Acc(0);
+  const int e0 = __ldg(A.row_ptr + i), e1 = __ldg(A.row_ptr + i + 1);
+  for (int e = e0 + sub; e < e1; e += L) acc = fma(Acc(__ldg(A.val + e)), Acc(x[__ldg(A.col + e)]), acc);
+  // the group's own lanes (they may leave the loop above at different times)
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned mask = L >= 32 ? 0xffffffffu : (((1u << L) - 1u) << (lane & ~(unsigned)(L - 1)));
+  for (int o = L >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, L);
+  return acc;
+}
+
 // The same row product with the operand given by a function of the column, so that a
 // vector which is a linear combination of stored ones (q = r - alpha s) need not be
 // written out before the product reads it at neighbouring rows.

@@ -175,6 +175,7 @@ __device__ __forceinline__ void gb_end_iteration(GapBound& S, double rn) {
 //               __syncthreads and the partials stay in shared memory.
 // Both give every thread of the team bit-identical reduction results.
 struct GridTeam {
+  int lanes = 1;  // one thread per row
   // Rows of this block: first, first + stride, ... below end.  Either one contiguous
   // chunk per block (neighbours within about a chunk are re-read from L1/L2 by the same
   // block), or grid-stride order: the whole grid sweeps a window of gridDim*blockDim
@@ -204,6 +205,7 @@ struct GridTeam {
 
 struct BlockTeam {
   int first, stride, end;
+  int lanes = 1;  // threads per row in the SpMVs of passes A and B (CSR; a power of two)
   double* smem;   // >= kWork + 3*kMaxDots doubles
   double* scal;   // >= 8 doubles of shared memory for scalar broadcasts
   __device__ __forceinline__ bool sync() { __syncthreads(); return true; }
@@ -225,6 +227,7 @@ struct BlockTeam {
 // in rank order through distributed shared memory -- identical totals in every block.
 struct ClusterTeam {
   int first, stride, end;
+  int lanes = 1;  // threads per row in the SpMVs of passes A and B (CSR; a power of two)
   unsigned rank, nrank;
   double* smem;   // >= kWork + 5*kMaxDots doubles
   double* scal;   // >= 8 doubles
@@ -386,6 +389,24 @@ __device__ bool replace_r2(const SolverParams<T, VR>& p, Team& team) {
   return true;
 }
 
+// y_i = (A x)_i for this block's rows with L threads per row (L = team.lanes): the block's
+// rows first + k*stride + [0, blockDim) are dealt to blockDim/L lane groups, so each
+// thread follows a chain of nnz/L dependent loads instead of nnz.  The block then reads
+// y at its own rows (one __syncthreads: no other block touches them).
+template <typename T, typename Team>
+__device__ void spmv_lanes(const Team& team, const MatView<T>& A, const T* x, T* y) {
+  const int L = team.lanes, G = blockDim.x / L, g = threadIdx.x / L, sub = threadIdx.x % L;
+  for (int base = team.first; base < team.end; base += team.stride)
+    for (int h = 0; h < L; ++h) {
+      const int i = base + g + h * G;
+      if (i < team.end) {
+        const T v = row_dot_lanes<T>(A, x, i, sub, L);
+        if (sub == 0) y[i] = v;
+      }
+    }
+  __syncthreads();
+}
+
 // The whole solve (Algorithm 2 + Eq. rr) for one system, executed by a team.
 template <bool AUTO, typename T, typename VR, typename Team>
 __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
@@ -508,6 +529,8 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     // ---------------- m_i = M^{-1} w_i (Neumann only; on the fly otherwise)
     if (neu && !neumann_apply(p, team, p.w, p.m, (const T*)nullptr, (T*)nullptr)) return;
     // ---------------- pass A: t_i = A m_i; lines 5-11; partials of line 12
+    const bool split = team.lanes > 1 && !neu && p.At.fmt == 0;   // lane-split SpMVs (batched CSR)
+    if (split) spmv_lanes(team, p.At, p.w, p.t);
     {
       const T aT = T(alpha), bT = T(beta), opT = T(omega_prev);
       Acc a_qy, a_yy;
@@ -521,7 +544,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         }
         const T wi = p.w[i];
         const T mi = neu ? p.m[i] : minv_local(p, wi, i);
-        const T ti = neu ? row_dot<T>(p.Au, p.m, i) : row_dot<T>(p.At, p.w, i);
+        const T ti = split ? p.t[i] : neu ? row_dot<T>(p.Au, p.m, i) : row_dot<T>(p.At, p.w, i);
         const T zo = p.z[i];
         const T np = neu ? p.nn[i] : (rep_last ? p.nb[i] : minv_local(p, zo, i));   // n_{i-1}
         const T kk = p.k[i], gg = p.g[i], ll = p.l[i], ss = p.s[i], vv = p.v[i], rr = p.r[i];
@@ -582,6 +605,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     if (p.rr_theta > 0.0 && rn <= rr_theta_thr) do_rr = true;
     if (do_auto) do_rr = true;
     // ---------------- pass B: v_i = A n_i; lines 17-20; partials of line 21
+    if (split) spmv_lanes(team, p.At, p.z, p.v);
     {
       const T aT = T(alpha), oT = T(omega);
       Acc a_rr, a_rw, a_rs, a_rz, a_r2;
@@ -598,7 +622,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         }
         const T zi = p.z[i];
         const T ni = neu ? p.nn[i] : minv_local(p, zi, i);
-        const T vi = neu ? row_dot<T>(p.Au, p.nn, i) : row_dot<T>(p.At, p.z, i);
+        const T vi = split ? p.v[i] : neu ? row_dot<T>(p.Au, p.nn, i) : row_dot<T>(p.At, p.z, i);
         const T wi = p.w[i];
         const T mi = neu ? p.m[i] : minv_local(p, wi, i);
         const T rr = p.r[i], ss = p.s[i], kk = p.k[i], ll = p.l[i], gg = p.g[i], ti = p.t[i];

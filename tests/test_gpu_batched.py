@@ -122,7 +122,7 @@ def test_batched_cluster_mixed_and_autotune_choice():
     assert info["n_ok"] == 30 and info["cluster_blocks"] == 4
     s2, _, _ = _batch_solver(bp, precision="mixed", tol=1e-8, max_it=500, rr_theta=1e-3)
     x2, info2 = s2.solve(b)   # autotune over one-block and cluster shapes
-    assert info2["n_ok"] == 30 and info2["cluster_blocks"] in (1, 2, 4, 8)
+    assert info2["n_ok"] == 30 and info2["cluster_blocks"] in (1, 2, 4, 8) and info2["lanes_per_row"] in (1, 2, 4, 8)
 
 
 def test_batched_cluster_option_rejected():
@@ -131,3 +131,33 @@ def test_batched_cluster_option_rejected():
     bp = tp.config4(nsys=3, n_lo=100, n_hi=200, band=16)
     with pytest.raises(pb.PBCGError):
         _batch_solver(bp, cluster_blocks=3)
+
+
+@pytest.mark.parametrize("lanes,cluster", [(2, 1), (4, 2), (8, 1)])
+def test_batched_lanes_per_row_matches_single_solver(lanes, cluster):
+    """Several threads per row in the SpMVs (shuffle-combined partial row sums) change only
+    the summation order: every system still matches the single-system solver."""
+    torch = torch_cuda()
+    from gpu_common import make_solver, gpu_solve
+    import paper_1809_01948_gb300 as pb
+    bp = tp.config4(nsys=10, n_lo=30, n_hi=5000, band=64)
+    c = bp.concat()
+    dev = torch.device("cuda:0")
+    s = pb.BatchSolver(c["row_off"], c["nnz_off"], torch.from_numpy(c["row_ptr"]).to(dev),
+                       torch.from_numpy(c["col"]).to(dev), torch.from_numpy(c["val"]).to(dev), precision="fp64",
+                       tol=1e-12, max_it=800, rr_period=50, grid_blocks=8 * cluster, block_threads=256,
+                       cluster_blocks=cluster, lanes_per_row=lanes)
+    b = torch.from_numpy(c["b"]).to(dev)
+    x, info = s.solve(b)
+    assert info["lanes_per_row"] == lanes and info["n_ok"] == 10, info["status"]
+    x = x.cpu().numpy()
+    for k, sysk in enumerate(bp.systems):
+        xk = x[c["row_off"][k]:c["row_off"][k + 1]]
+        single = make_solver(tp.Problem("s", sysk.A, sysk.b, sysk.x0, None, precond="jacobi", fmt="csr"),
+                             tol=1e-12, max_it=800, rr_period=50)
+        xs, res, _, _ = gpu_solve(single, sysk.b)
+        assert res.status == 0
+        assert np.linalg.norm(xk - xs) <= 1e-10 * np.linalg.norm(xs)
+    with pytest.raises(pb.PBCGError):
+        pb.BatchSolver(c["row_off"], c["nnz_off"], torch.from_numpy(c["row_ptr"]).to(dev),
+                       torch.from_numpy(c["col"]).to(dev), torch.from_numpy(c["val"]).to(dev), lanes_per_row=3)
