@@ -69,6 +69,8 @@ __device__ void build_params(const BatchDev& d, int k, SolverParams<T, VR>& p) {
   p.A64 = csr_view<VR>(n, rp, col, (const VR*)d.valR + e0);
   p.dinv = d.dinv ? (const T*)d.dinv + r0 : nullptr;
   p.dinv_c = T(0);
+  p.scalar_prec = 0;
+  p.dinv_x = 0.0;
   p.prefetch = 0;
   p.prec = d.prec;
   p.degree = 0;

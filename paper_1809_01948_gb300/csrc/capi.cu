@@ -144,6 +144,28 @@ __global__ void max_u64_kernel(int n, const unsigned long long* v, unsigned long
   warp_atomic_max(out, i < n ? v[i] : 0ull);
 }
 
+// Smallest and largest diagonal entry as order-preserving integer images (warp-reduced).
+__device__ __forceinline__ unsigned long long ordered_u64(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__global__ void diag_range_kernel(int n, const double* diag, unsigned long long* range) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long lo = ~0ull, hi = 0ull;
+  if (i < n) lo = hi = ordered_u64(diag[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o), b = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (lo != ~0ull) atomicMin(range, lo);
+    if (hi != 0ull) atomicMax(range + 1, hi);
+  }
+}
+
 template <typename T>
 __global__ void dinv_max_kernel(int n, const T* dinv, unsigned long long* bits) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -431,6 +453,23 @@ static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
   const size_t es = elem_size(c->precision);
   const bool mixed = c->precision == PBCG_MIXED;
   if (need_diag) {
+    // a constant diagonal makes Jacobi a scalar preconditioner (SolverParams::scalar_prec)
+    unsigned long long* rng = nullptr;
+    CK(cudaMalloc(&rng, 2 * sizeof(unsigned long long)), "cudaMalloc");
+    const unsigned long long init[2] = {~0ull, 0ull};
+    CK(cudaMemcpyAsync(rng, init, sizeof init, cudaMemcpyHostToDevice, c->stream), "copy");
+    diag_range_kernel<<<nb, 256, 0, c->stream>>>(n, c->diag64, rng);
+    unsigned long long hr[2];
+    CK(cudaMemcpyAsync(hr, rng, sizeof hr, cudaMemcpyDeviceToHost, c->stream), "copy");
+    CK(cudaStreamSynchronize(c->stream), "diagonal range");
+    cudaFree(rng);
+    if (hr[0] == hr[1]) {
+      const unsigned long long u = (hr[0] >> 63) ? (hr[0] & 0x7fffffffffffffffull) : ~hr[0];
+      double d;
+      memcpy(&d, &u, sizeof d);
+      c->dconst = 1;
+      c->dconst_inv = 1.0 / d;
+    }
     CK(cudaMalloc(&c->dinv64, sizeof(double) * n), "cudaMalloc dinv");
     dinv_kernel<<<nb, 256, 0, c->stream>>>(n, c->diag64, c->dinv64);
     if (mixed) {

@@ -71,6 +71,8 @@ struct pbcg_ctx {
   double st_val[kMaxDiag] = {0};         // A's value at each offset
   double st_dinv = 0.0;                  // 1 / (the constant diagonal)
   unsigned short* st_mask = nullptr;     // per row: bit d set when the entry at st_off[d] is present
+  int dconst = 0;            // the diagonal is one value d (every row, non-zero)
+  double dconst_inv = 0.0;   // 1 / d
   double norm_bound = 0.0;   // sqrt(||A||_1 ||A||_inf) (upper bound of ||A||_2)
   double dinv_max = 1.0;     // max |d_inv| in the working precision (1 without preconditioner)
   // vectors + reductions
@@ -175,6 +177,8 @@ inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int 
   p.dinv = (c->prec_kind == PBCG_PREC_NONE || c->stencil) ? nullptr
            : (std::is_same<T, float>::value ? (const T*)c->dinvT : (const T*)c->dinv64);
   p.dinv_c = T(c->st_dinv);
+  p.scalar_prec = (c->prec_kind == PBCG_PREC_JACOBI && c->dconst && !c->opt.rr_auto) ? 1 : 0;
+  p.dinv_x = c->dconst_inv;
   p.prec = c->prec_kind;
   p.degree = c->degree;
   p.b = b;

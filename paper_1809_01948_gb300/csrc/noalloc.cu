@@ -36,7 +36,32 @@ struct NoAllocState {
   double true_rel;
   int flags;
   int reserved;
+  unsigned long long drange[2];   // smallest / largest diagonal entry (order-preserving images)
 };
+static_assert(sizeof(NoAllocState) <= 256, "the scratch reserves 256 bytes for the state");
+
+// Smallest and largest diagonal entry, as the context-based solver computes them: with a
+// constant diagonal both entry points run Jacobi in the same scaled form.
+__device__ __forceinline__ unsigned long long na_ordered(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__global__ void na_diag_range(int n, const double* diag, unsigned long long* range) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long lo = ~0ull, hi = 0ull;
+  if (i < n) lo = hi = na_ordered(diag[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o), b = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (lo != ~0ull) atomicMin(range, lo);
+    if (hi != 0ull) atomicMax(range + 1, hi);
+  }
+}
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
@@ -214,9 +239,25 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   if (h.flags & 2) return set_error(PBCG_INVALID_ARG, "CSR column index out of range or not increasing");
   if (h.flags & 4) return set_error(PBCG_INVALID_ARG, "matrix has a non-finite value");
   if (h.flags & 8) return set_error(PBCG_INVALID_ARG, "Jacobi needs a non-zero diagonal");
+  bool dconst = false;
+  double dconst_inv = 0.0;
   if (jac) {
     na_fold<<<nb, 256, 0, s>>>(A64, diag, dinv, fold);
     NCK(cudaGetLastError(), "fold launch");
+    const unsigned long long init[2] = {~0ull, 0ull};
+    NCK(cudaMemcpyAsync(state->drange, init, sizeof init, cudaMemcpyHostToDevice, s), "copy");
+    na_diag_range<<<nb, 256, 0, s>>>(n, diag, state->drange);
+    NCK(cudaGetLastError(), "diagonal range launch");
+    unsigned long long hr[2];
+    NCK(cudaMemcpyAsync(hr, state->drange, sizeof hr, cudaMemcpyDeviceToHost, s), "copy");
+    NCK(cudaStreamSynchronize(s), "diagonal range");
+    if (hr[0] == hr[1]) {
+      const unsigned long long u = (hr[0] >> 63) ? (hr[0] & 0x7fffffffffffffffull) : ~hr[0];
+      double d;
+      memcpy(&d, &u, sizeof d);
+      dconst = true;
+      dconst_inv = 1.0 / d;
+    }
   }
   // launch shape: the same rule as the context-based solver
   const int nt = opt->block_threads ? opt->block_threads : 512;
@@ -248,6 +289,8 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
     p.At = A64;
   }
   p.dinv = jac ? dinv : nullptr;
+  p.scalar_prec = (jac && dconst) ? 1 : 0;
+  p.dinv_x = dconst_inv;
   p.prec = M->kind;
   p.b = b;
   p.x = x;

@@ -46,6 +46,11 @@ struct SolverParams {
                         // and replacement residuals, evaluated in FP64
   const T* dinv;        // D^{-1} (nullptr without preconditioner or when D is constant)
   T dinv_c;             // D^{-1} of a constant diagonal (used when dinv is nullptr)
+  // 1: Jacobi with a constant diagonal d, run in scaled form (see minv_local): every
+  // preconditioned vector (k, g, l, m, n, u) is kept multiplied by d, and the 1/d moves
+  // into the x update and the replacement's s = A g (dinv_x = 1/d in FP64)
+  int scalar_prec;
+  double dinv_x;
   int prec;             // 0 none, 1 Jacobi, 2 Neumann
   int degree;
   const double* b;
@@ -270,9 +275,17 @@ __device__ __forceinline__ T dinv_at(const SolverParams<T, VR>& p, int i) {
   return p.dinv ? __ldg(p.dinv + i) : p.dinv_c;
 }
 
+// M^{-1} v at row i.  With a constant diagonal d (scalar_prec) the Jacobi preconditioner
+// is the scalar 1/d, and Algorithm 2 with M^{-1} = I/d equals Algorithm 2 with M^{-1} = I
+// on every vector the reductions and the stop test see (r, w, s, z, t, v, q, y; alpha,
+// beta, omega unchanged), while its preconditioned vectors are the identity version's
+// divided by d.  The solver therefore keeps those vectors multiplied by d -- this function
+// is then the identity -- and applies the 1/d where they leave the recurrences: in the
+// x update (x += (alpha/d) g + (omega/d) u) and in the replacement's s = A g.  Exact
+// arithmetic is unchanged; two FP64 multiplications per row and pass disappear.
 template <typename T, typename VR>
 __device__ __forceinline__ T minv_local(const SolverParams<T, VR>& p, T v, int i) {
-  return p.prec == 1 ? T(dinv_at(p, i) * v) : v;
+  return (p.prec == 1 && !p.scalar_prec) ? T(dinv_at(p, i) * v) : v;
 }
 
 // Neumann polynomial M^{-1} src = sum_{j<=d} (I - D^{-1}A)^j D^{-1} src by d
@@ -333,7 +346,8 @@ __device__ void replace_r1(const SolverParams<T, VR>& p, Team& team, bool write)
     const double r64 = p.b[i] - row_dot<double>(p.A64, p.x, i);
     if (write) {
       const T ri = T(r64);
-      const T si = T(row_dot<double>(p.A64, p.g, i));
+      const double ag = row_dot<double>(p.A64, p.g, i);
+      const T si = T(p.scalar_prec ? ag * p.dinv_x : ag);
       p.r[i] = ri;
       p.s[i] = si;
       if (!neu) {
@@ -608,6 +622,8 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     if (split) spmv_lanes(team, p.At, p.z, p.v);
     {
       const T aT = T(alpha), oT = T(omega);
+      const double ax = p.scalar_prec ? alpha * p.dinv_x : alpha;   // x update (see minv_local)
+      const double ox = p.scalar_prec ? omega * p.dinv_x : omega;
       Acc a_rr, a_rw, a_rs, a_rz, a_r2;
       DAcc a_xn;
       Acc a_nn, a_vn;   // AUTO: squared norms of x_i, n_i, v_i
@@ -631,7 +647,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         const T y = fma(-aT, zi, wi);
         const double xo = p.x[i];
         if (AUTO) { a_xn.add(xo, xo); a_nn.add(ni, ni); a_vn.add(vi, vi); }
-        const double xn = fma(omega, (double)u, fma(alpha, (double)gg, xo));  // line 17
+        const double xn = fma(ox, (double)u, fma(ax, (double)gg, xo));  // line 17
         const T rn1 = fma(-oT, y, q);                    // r_{i+1} = q_i - omega_i y_i
         const T kn = fma(-oT, fma(-aT, ni, mi), u);      // k_{i+1} = u_i - omega_i (m_i - alpha_i n_i)
         const T wn = fma(-oT, fma(-aT, vi, ti), y);      // w_{i+1} = y_i - omega_i (t_i - alpha_i v_i)
@@ -965,13 +981,15 @@ __device__ void classic_body(const SolverParams<T, VR>& p, Team& team) {
     // lines 13-15: x_{i+1} = (x_i + alpha g_i) + omega u_i, r_{i+1} = q_i - omega y_i, (r0, r_{i+1})
     {
       const T aT = T(alpha), oT = T(omega);
+      const double ax = p.scalar_prec ? alpha * p.dinv_x : alpha;   // x update (see minv_local)
+      const double ox = p.scalar_prec ? omega * p.dinv_x : omega;
       Acc a_rr, a_r2;
       const bool hist = it < p.K;
       CL_ROWS {
         const T qi = fma(-aT, s_new[i], p.r[i]);
         const T gi = minv_local(p, p_new[i], i);
         const T ui = minv_local(p, qi, i);
-        const double xn = fma(omega, (double)ui, fma(alpha, (double)gi, p.x[i]));
+        const double xn = fma(ox, (double)ui, fma(ax, (double)gi, p.x[i]));
         const T rn1 = fma(-oT, y[i], qi);
         p.x[i] = xn;
         p.r[i] = rn1;
