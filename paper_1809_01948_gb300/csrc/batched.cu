@@ -69,8 +69,7 @@ __device__ void build_params(const BatchDev& d, int k, SolverParams<T, VR>& p) {
   p.A64 = csr_view<VR>(n, rp, col, (const VR*)d.valR + e0);
   p.dinv = d.dinv ? (const T*)d.dinv + r0 : nullptr;
   p.dinv_c = T(0);
-  p.scalar_prec = 0;
-  p.dinv_x = 0.0;
+  p.dinv_x = 1.0;
   p.prefetch = 0;
   p.prec = d.prec;
   p.degree = 0;
@@ -122,7 +121,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev 
     team.lanes = d.lanes;
     team.smem = smem;
     team.scal = scal;
-    solve_body<false>(p, team);
+    solve_body<false, false>(p, team);
     __syncthreads();
     // final FP64 true residual of this system
     double a[2] = {0.0, 0.0};
@@ -185,7 +184,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_cluster_kernel(const B
     team.first = (int)rank * blockDim.x;
     team.stride = (int)nrank * blockDim.x;
     team.end = n;
-    solve_body<false>(p, team);
+    solve_body<false, false>(p, team);
     team.sync();
     // final FP64 true residual of this system
     double a[2] = {0.0, 0.0};

@@ -346,12 +346,16 @@ static bool streaming(const pbcg_ctx* c) {
 template <typename T>
 static const void* kernel_ptr(const pbcg_ctx* c) {
   const pbcg_options& o = c->opt;
+  const bool sc = scalar_jacobi(c);
   if constexpr (std::is_same<T, double>::value) {
-    if (o.method == PBCG_CLASSIC) return (const void*)classic_kernel<double>;
+    if (o.method == PBCG_CLASSIC)
+      return sc ? (const void*)classic_kernel<double, true> : (const void*)classic_kernel<double, false>;
   } else {
-    if (streaming(c)) return (const void*)pbicgstab_kernel<float, false, true>;
+    if (streaming(c))
+      return sc ? (const void*)pbicgstab_kernel<float, false, true, true> : (const void*)pbicgstab_kernel<float, false, true>;
   }
-  return o.rr_auto ? (const void*)pbicgstab_kernel<T, true> : (const void*)pbicgstab_kernel<T, false>;
+  if (o.rr_auto) return (const void*)pbicgstab_kernel<T, true>;
+  return sc ? (const void*)pbicgstab_kernel<T, false, false, true> : (const void*)pbicgstab_kernel<T, false>;
 }
 
 // Default shape: the solver kernels' register budgets (SolverLaunch): one 1024-thread block
@@ -453,7 +457,7 @@ static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
   const size_t es = elem_size(c->precision);
   const bool mixed = c->precision == PBCG_MIXED;
   if (need_diag) {
-    // a constant diagonal makes Jacobi a scalar preconditioner (SolverParams::scalar_prec)
+    // a constant diagonal makes Jacobi a scalar preconditioner (the SCALAR kernel builds)
     unsigned long long* rng = nullptr;
     CK(cudaMalloc(&rng, 2 * sizeof(unsigned long long)), "cudaMalloc");
     const unsigned long long init[2] = {~0ull, 0ull};

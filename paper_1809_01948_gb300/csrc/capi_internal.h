@@ -153,6 +153,11 @@ int l2_bytes();   // L2 size of the current device in bytes
 
 // Bytes an iteration streams repeatedly: the work vectors it touches (about 12), x, and
 // the operator (the stencil mask, or the stored values and indices).
+// Jacobi with a constant diagonal runs in scaled form (the SCALAR kernel builds).
+inline bool scalar_jacobi(const pbcg_ctx* c) {
+  return c->prec_kind == PBCG_PREC_JACOBI && c->dconst && !c->opt.rr_auto;
+}
+
 inline double hot_bytes(const pbcg_ctx* c) {
   const double es = (double)elem_size(c->precision);
   double op;
@@ -177,8 +182,7 @@ inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int 
   p.dinv = (c->prec_kind == PBCG_PREC_NONE || c->stencil) ? nullptr
            : (std::is_same<T, float>::value ? (const T*)c->dinvT : (const T*)c->dinv64);
   p.dinv_c = T(c->st_dinv);
-  p.scalar_prec = (c->prec_kind == PBCG_PREC_JACOBI && c->dconst && !c->opt.rr_auto) ? 1 : 0;
-  p.dinv_x = c->dconst_inv;
+  p.dinv_x = c->dconst ? c->dconst_inv : 1.0;
   p.prec = c->prec_kind;
   p.degree = c->degree;
   p.b = b;

@@ -262,8 +262,11 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   // launch shape: the same rule as the context-based solver
   const int nt = opt->block_threads ? opt->block_threads : 512;
   if (nt < 32 || nt > kMaxThreads || nt % 32) return set_error(PBCG_INVALID_ARG, "bad block_threads");
+  // Jacobi with a constant diagonal runs the scaled-form build
+  const void* kern = (jac && dconst) ? (const void*)pbicgstab_kernel<double, false, false, true>
+                                     : (const void*)pbicgstab_kernel<double, false>;
   int per_sm = 0;
-  NCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)pbicgstab_kernel<double, false>, nt, 0), "occupancy");
+  NCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, 0), "occupancy");
   const int sms = sm_count();
   const int max_co = std::min(per_sm * sms, kMaxGrid);
   int grid = opt->grid_blocks;
@@ -289,8 +292,7 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
     p.At = A64;
   }
   p.dinv = jac ? dinv : nullptr;
-  p.scalar_prec = (jac && dconst) ? 1 : 0;
-  p.dinv_x = dconst_inv;
+  p.dinv_x = (jac && dconst) ? dconst_inv : 1.0;
   p.prec = M->kind;
   p.b = b;
   p.x = x;
@@ -317,7 +319,7 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   else for (int d = 0; d < A64.ndiag; ++d) bandwidth = std::max(bandwidth, std::abs(A64.off[d]));
   p.strided = bandwidth > p.chunk / 2 ? 1 : 0;
   void* args[] = {&p};
-  NCK(cudaLaunchCooperativeKernel((const void*)pbicgstab_kernel<double, false>, grid, nt, args, 0, s), "cooperative launch");
+  NCK(cudaLaunchCooperativeKernel(kern, grid, nt, args, 0, s), "cooperative launch");
   na_true_res<<<1, 1024, 0, s>>>(A64, b, x, &state->true_rel);
   NCK(cudaGetLastError(), "true residual launch");
   NCK(cudaMemcpyAsync(&h, state, sizeof h, cudaMemcpyDeviceToHost, s), "copy result");

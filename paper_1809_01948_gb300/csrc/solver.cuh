@@ -46,11 +46,7 @@ struct SolverParams {
                         // and replacement residuals, evaluated in FP64
   const T* dinv;        // D^{-1} (nullptr without preconditioner or when D is constant)
   T dinv_c;             // D^{-1} of a constant diagonal (used when dinv is nullptr)
-  // 1: Jacobi with a constant diagonal d, run in scaled form (see minv_local): every
-  // preconditioned vector (k, g, l, m, n, u) is kept multiplied by d, and the 1/d moves
-  // into the x update and the replacement's s = A g (dinv_x = 1/d in FP64)
-  int scalar_prec;
-  double dinv_x;
+  double dinv_x;        // 1/d of a constant diagonal, for the scaled-form (SCALAR) kernels
   int prec;             // 0 none, 1 Jacobi, 2 Neumann
   int degree;
   const double* b;
@@ -275,7 +271,7 @@ __device__ __forceinline__ T dinv_at(const SolverParams<T, VR>& p, int i) {
   return p.dinv ? __ldg(p.dinv + i) : p.dinv_c;
 }
 
-// M^{-1} v at row i.  With a constant diagonal d (scalar_prec) the Jacobi preconditioner
+// M^{-1} v at row i.  With a constant diagonal d (SCALAR kernels) the Jacobi preconditioner
 // is the scalar 1/d, and Algorithm 2 with M^{-1} = I/d equals Algorithm 2 with M^{-1} = I
 // on every vector the reductions and the stop test see (r, w, s, z, t, v, q, y; alpha,
 // beta, omega unchanged), while its preconditioned vectors are the identity version's
@@ -283,9 +279,9 @@ __device__ __forceinline__ T dinv_at(const SolverParams<T, VR>& p, int i) {
 // is then the identity -- and applies the 1/d where they leave the recurrences: in the
 // x update (x += (alpha/d) g + (omega/d) u) and in the replacement's s = A g.  Exact
 // arithmetic is unchanged; two FP64 multiplications per row and pass disappear.
-template <typename T, typename VR>
+template <bool SCALAR, typename T, typename VR>
 __device__ __forceinline__ T minv_local(const SolverParams<T, VR>& p, T v, int i) {
-  return (p.prec == 1 && !p.scalar_prec) ? T(dinv_at(p, i) * v) : v;
+  return (p.prec == 1 && !SCALAR) ? T(dinv_at(p, i) * v) : v;
 }
 
 // Neumann polynomial M^{-1} src = sum_{j<=d} (I - D^{-1}A)^j D^{-1} src by d
@@ -335,7 +331,7 @@ __device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T*
 // nb = D^{-1} z_i (n_i stays the one computed from the old z_i, reading R6).
 // Publishes the partial ||b - A x||^2 to P2.  With write == false only the norm
 // is computed (stopping-test verification).
-template <bool AUTO, typename T, typename VR, typename Team>
+template <bool AUTO, bool SCALAR, typename T, typename VR, typename Team>
 __device__ void replace_r1(const SolverParams<T, VR>& p, Team& team, bool write) {
   using Acc = typename AccOf<T>::type;
   const int row0 = team.first, rstride = team.stride, row1 = team.end;
@@ -347,14 +343,14 @@ __device__ void replace_r1(const SolverParams<T, VR>& p, Team& team, bool write)
     if (write) {
       const T ri = T(r64);
       const double ag = row_dot<double>(p.A64, p.g, i);
-      const T si = T(p.scalar_prec ? ag * p.dinv_x : ag);
+      const T si = T(SCALAR ? ag * p.dinv_x : ag);
       p.r[i] = ri;
       p.s[i] = si;
       if (!neu) {
-        const T ki = minv_local(p, ri, i), li = minv_local(p, si, i);
+        const T ki = minv_local<SCALAR>(p, ri, i), li = minv_local<SCALAR>(p, si, i);
         p.k[i] = ki;
         p.l[i] = li;
-        p.nb[i] = minv_local(p, p.z[i], i);
+        p.nb[i] = minv_local<SCALAR>(p, p.z[i], i);
         if (AUTO) { a_k.add(ki, ki); a_l.add(li, li); }
       }
       if (AUTO) {
@@ -422,7 +418,7 @@ __device__ void spmv_lanes(const Team& team, const MatView<T>& A, const T* x, T*
 }
 
 // The whole solve (Algorithm 2 + Eq. rr) for one system, executed by a team.
-template <bool AUTO, typename T, typename VR, typename Team>
+template <bool AUTO, bool SCALAR, typename T, typename VR, typename Team>
 __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   using Acc = typename AccOf<T>::type;
   const int n = p.n;
@@ -473,7 +469,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       const T ri = T(r64);
       p.r[i] = ri;
       p.rh[i] = ri;
-      if (!neu) p.k[i] = minv_local(p, ri, i);
+      if (!neu) p.k[i] = minv_local<SCALAR>(p, ri, i);
       p.g[i] = T(0); p.s[i] = T(0); p.l[i] = T(0); p.z[i] = T(0); p.v[i] = T(0);
       if (neu) p.nn[i] = T(0);
       a_rr.add(ri, ri);
@@ -557,10 +553,10 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
           if (neu) { prefetch_l2(p.m + j); prefetch_l2(p.nn + j); }
         }
         const T wi = p.w[i];
-        const T mi = neu ? p.m[i] : minv_local(p, wi, i);
+        const T mi = neu ? p.m[i] : minv_local<SCALAR>(p, wi, i);
         const T ti = split ? p.t[i] : neu ? row_dot<T>(p.Au, p.m, i) : row_dot<T>(p.At, p.w, i);
         const T zo = p.z[i];
-        const T np = neu ? p.nn[i] : (rep_last ? p.nb[i] : minv_local(p, zo, i));   // n_{i-1}
+        const T np = neu ? p.nn[i] : (rep_last ? p.nb[i] : minv_local<SCALAR>(p, zo, i));   // n_{i-1}
         const T kk = p.k[i], gg = p.g[i], ll = p.l[i], ss = p.s[i], vv = p.v[i], rr = p.r[i];
         const T gn = fma(bT, fma(-opT, ll, gg), kk);   // g_i = k_i + beta_i (g_{i-1} - omega_{i-1} l_{i-1})
         const T sn = fma(bT, fma(-opT, zo, ss), wi);   // s_i = w_i + beta_i (s_{i-1} - omega_{i-1} z_{i-1})
@@ -622,8 +618,8 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     if (split) spmv_lanes(team, p.At, p.z, p.v);
     {
       const T aT = T(alpha), oT = T(omega);
-      const double ax = p.scalar_prec ? alpha * p.dinv_x : alpha;   // x update (see minv_local)
-      const double ox = p.scalar_prec ? omega * p.dinv_x : omega;
+      const double ax = SCALAR ? alpha * p.dinv_x : alpha;   // x update (see minv_local)
+      const double ox = SCALAR ? omega * p.dinv_x : omega;
       Acc a_rr, a_rw, a_rs, a_rz, a_r2;
       DAcc a_xn;
       Acc a_nn, a_vn;   // AUTO: squared norms of x_i, n_i, v_i
@@ -637,10 +633,10 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
           if (neu) { prefetch_l2(p.m + j); prefetch_l2(p.nn + j); }
         }
         const T zi = p.z[i];
-        const T ni = neu ? p.nn[i] : minv_local(p, zi, i);
+        const T ni = neu ? p.nn[i] : minv_local<SCALAR>(p, zi, i);
         const T vi = split ? p.v[i] : neu ? row_dot<T>(p.Au, p.nn, i) : row_dot<T>(p.At, p.z, i);
         const T wi = p.w[i];
-        const T mi = neu ? p.m[i] : minv_local(p, wi, i);
+        const T mi = neu ? p.m[i] : minv_local<SCALAR>(p, wi, i);
         const T rr = p.r[i], ss = p.s[i], kk = p.k[i], ll = p.l[i], gg = p.g[i], ti = p.t[i];
         const T q = fma(-aT, ss, rr);
         const T u = fma(-aT, ll, kk);
@@ -670,7 +666,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     // ---------------- residual replacement, Eq. (rr), after line 20 (reading R6)
     if (do_rr) {
       PBCG_SYNC();
-      replace_r1<AUTO>(p, team, true);
+      replace_r1<AUTO, SCALAR>(p, team, true);
       PBCG_SYNC();
       if (!replace_r2<AUTO>(p, team)) return;
       ++nrep;
@@ -704,7 +700,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       // reading R5: verify with the FP64 true residual; with a replacement policy a
       // failed check forces a replacement, without one the solve has stagnated.
       const bool any_rr = p.rr_period > 0 || p.rr_theta > 0.0 || AUTO;
-      replace_r1<AUTO>(p, team, any_rr);
+      replace_r1<AUTO, SCALAR>(p, team, any_rr);
       PBCG_SYNC();
       double t1[6];
       if (AUTO) team.template combine<6>(2, t1);
@@ -793,7 +789,7 @@ struct SolverLaunch {
 
 // One cooperative grid solves one system.  AUTO adds the automated replacement policy
 // (extra norms in the reductions and the gap bound in thread 0).
-template <typename T, bool AUTO, bool STREAM = false>
+template <typename T, bool AUTO, bool STREAM = false, bool SCALAR = false>
 __global__ void __launch_bounds__(SolverLaunch<T, STREAM>::kThreads, SolverLaunch<T, STREAM>::kBlocksPerSM)
     pbicgstab_kernel(const SolverParams<T> p) {
   __shared__ double smem[kWork + 3 * kMaxDots];
@@ -817,7 +813,7 @@ __global__ void __launch_bounds__(SolverLaunch<T, STREAM>::kThreads, SolverLaunc
   team.part = p.part;
   team.smem = smem;
   team.scal = scal;
-  solve_body<AUTO>(p, team);
+  solve_body<AUTO, SCALAR>(p, team);
 }
 
 // Several independent solves that share the grid: team t is blocks
@@ -852,7 +848,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pbicgstab_multi_kernel(const S
   team.part = sp.part;
   team.smem = smem;
   team.scal = scal;
-  solve_body<false>(sp, team);
+  solve_body<false, false>(sp, team);
 }
 
 // ---------------------------------------------------------------------------
@@ -865,7 +861,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pbicgstab_multi_kernel(const S
 // neighbouring rows while writing the new ones.  No preconditioner or Jacobi (folded
 // into A D^{-1}: s = A g = (A D^{-1}) p, y = A u = (A D^{-1}) q); no replacement.
 // Vector slots: r, rh, y = w, p = g / l (alternating), s = s / z (alternating).
-template <typename T, typename VR, typename Team>
+template <bool SCALAR, typename T, typename VR, typename Team>
 __device__ void classic_body(const SolverParams<T, VR>& p, Team& team) {
   using Acc = typename AccOf<T>::type;
   const int n = p.n;
@@ -981,14 +977,14 @@ __device__ void classic_body(const SolverParams<T, VR>& p, Team& team) {
     // lines 13-15: x_{i+1} = (x_i + alpha g_i) + omega u_i, r_{i+1} = q_i - omega y_i, (r0, r_{i+1})
     {
       const T aT = T(alpha), oT = T(omega);
-      const double ax = p.scalar_prec ? alpha * p.dinv_x : alpha;   // x update (see minv_local)
-      const double ox = p.scalar_prec ? omega * p.dinv_x : omega;
+      const double ax = SCALAR ? alpha * p.dinv_x : alpha;   // x update (see minv_local)
+      const double ox = SCALAR ? omega * p.dinv_x : omega;
       Acc a_rr, a_r2;
       const bool hist = it < p.K;
       CL_ROWS {
         const T qi = fma(-aT, s_new[i], p.r[i]);
-        const T gi = minv_local(p, p_new[i], i);
-        const T ui = minv_local(p, qi, i);
+        const T gi = minv_local<SCALAR>(p, p_new[i], i);
+        const T ui = minv_local<SCALAR>(p, qi, i);
         const double xn = fma(ox, (double)ui, fma(ax, (double)gi, p.x[i]));
         const T rn1 = fma(-oT, y[i], qi);
         p.x[i] = xn;
@@ -1048,7 +1044,7 @@ __device__ void classic_body(const SolverParams<T, VR>& p, Team& team) {
 #undef CL_FINISH
 }
 
-template <typename T>
+template <typename T, bool SCALAR = false>
 __global__ void __launch_bounds__(kMaxThreads, 1) classic_kernel(const SolverParams<T> p) {
   __shared__ double smem[kWork + 3 * kMaxDots];
   __shared__ double scal[8];
@@ -1071,7 +1067,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) classic_kernel(const SolverPar
   team.part = p.part;
   team.smem = smem;
   team.scal = scal;
-  classic_body(p, team);
+  classic_body<SCALAR>(p, team);
 }
 
 }  // namespace pbcg
