@@ -187,13 +187,13 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    if args.workload == "c2":
-        prob = tp.config2(args.grid or GRID)
+    if args.workload == "convdiff2d":
+        prob = tp.problem_convdiff2d(args.grid or GRID)
         off, data = tp.csr_to_dia(prob.A)
         mat = dict(offsets=off.tolist(), dia=torch.from_numpy(data).to(dev), precond="jacobi")
         workload = "convdiff2d_%dx%d_dia5_jacobi_tol1e-10" % ((args.grid or GRID), (args.grid or GRID))
     else:
-        prob = tp.config3(args.grid or 256)
+        prob = tp.problem_convdiff3d(args.grid or 256)
         mat = dict(row_ptr=torch.from_numpy(prob.A.row_ptr).to(dev), col=torch.from_numpy(prob.A.col).to(dev),
                    val=torch.from_numpy(prob.A.val).to(dev), precond="neumann", degree=2)
         workload = "convdiff3d_%d^3_csr7_neumann2_tol1e-10" % (args.grid or 256)
@@ -203,7 +203,7 @@ def run_gpu(args):
         "fp64": dict(precision="fp64", rr_period=100, rr_theta=0.0),
         "mixed": dict(precision="mixed", rr_period=args.mixed_period, rr_theta=args.theta),
     }
-    if args.workload == "c2":
+    if args.workload == "convdiff2d":
         # Algorithm 1, the paper's reference method, on the same system (three reduction
         # phases per iteration instead of two)
         variants["classic"] = dict(precision="fp64", method="classic", rr_period=0, rr_theta=0.0)
@@ -274,7 +274,7 @@ def run_gpu(args):
 
     # roofline of the dominant kernel (the persistent solver), per launch
     prec = args.precision
-    bpr = (bytes_per_row_iteration(prec, storage=storage) if args.workload == "c2"
+    bpr = (bytes_per_row_iteration(prec, storage=storage) if args.workload == "convdiff2d"
            else bytes_per_row_iteration_neumann(prec, storage=storage))
     alg_bytes = n * (bpr * head["iterations"] + bytes_per_row_replacement(prec, storage=storage) * head["n_replacements"])
     kernel_s = head["kernel_ms"] * 1e-3
@@ -292,7 +292,7 @@ def run_gpu(args):
            "bytes_per_row_iteration": bpr}
     # the same time against the byte model of the general (CSR / DIA values) storage, which
     # the stencil storage undercuts: the effective bandwidth of the solve
-    gen = (bytes_per_row_iteration(prec, storage="general") if args.workload == "c2"
+    gen = (bytes_per_row_iteration(prec, storage="general") if args.workload == "convdiff2d"
            else bytes_per_row_iteration_neumann(prec, storage="general"))
     gen_bytes = n * (gen * head["iterations"] + bytes_per_row_replacement(prec, storage="general") * head["n_replacements"])
     hbm["general_storage_model"] = {"bytes_per_row_iteration": gen,
@@ -300,7 +300,7 @@ def run_gpu(args):
                                     "frac": round(gen_bytes / kernel_s / 1e9 / hbm_peak, 4)}
     if prec == "fp64":
         # FP64 pipe bound: GB300 runs FP64 at 1/58 of FP32; nominal 1.25 TFLOP/s (measured DFMA 1.197)
-        fpr = fp64_flops_per_row_iteration() if args.workload == "c2" else fp64_flops_per_row_iteration_neumann()
+        fpr = fp64_flops_per_row_iteration() if args.workload == "convdiff2d" else fp64_flops_per_row_iteration_neumann()
         ach = fpr * n * head["iterations"] / kernel_s / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": 1.25, "unit": "TFLOP/s",
                 "frac": round(ach / 1.25, 4), "traffic": traffic,
@@ -311,11 +311,11 @@ def run_gpu(args):
                 "frac": hbm["frac"], "traffic": traffic, "peak_source": hbm["peak_source"],
                 "bytes_per_row_iteration": bpr, "general_storage_model": hbm["general_storage_model"],
                 }
-        if args.workload == "c2":
+        if args.workload == "convdiff2d":
             roof["note"] = "working set is L2-resident across iterations (DRAM traffic ~3 B/row/it)"
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and args.workload == "c2":
+    if rank == 0 and world == 1 and not args.no_cpu and args.workload == "convdiff2d":
         cpu = cpu_baseline(args, head["iterations"], sample_iters=args.cpu_iters)
 
     if rank == 0:
@@ -325,7 +325,7 @@ def run_gpu(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
             "config": {"workload": workload, "n": n,
-                       "format": "DIA 5 diagonals FP64" if args.workload == "c2" else "CSR int32, 7 nnz/row, FP64 values",
+                       "format": "DIA 5 diagonals FP64" if args.workload == "convdiff2d" else "CSR int32, 7 nnz/row, FP64 values",
                        "operator_storage": storage + (" (constant coefficients detected at create: one value per "
                                                       "offset + 16-bit row mask)" if storage == "stencil" else ""),
                        "precision": prec, "replacement": variants[prec], "global_batch": 1 * world,
@@ -352,7 +352,7 @@ sys.path.insert(0, %(root)r)
 import numpy as np
 import testproblems as tp
 from oracle import krylov
-prob = tp.config2(%(grid)d)
+prob = tp.problem_convdiff2d(%(grid)d)
 A = prob.A.to_scipy()
 t0 = time.perf_counter()
 r = krylov.pbicgstab(A, prob.b, precond="jacobi", tol=1e-300, maxit=%(iters)d, rr_period=100)
@@ -413,7 +413,7 @@ def _hbm_peak():
 
 
 def run_batched(args):
-    """Configuration 4: 512 independent random banded systems (N_k ~ U[2048, 65536], 7-15
+    """Batched workload: 512 independent random banded systems (N_k ~ U[2048, 65536], 7-15
     non-zeros per row, FP32 values), mixed precision, Jacobi, tol 1e-8, one persistent
     launch replayed from a CUDA graph.  A step is one batch solve of all systems."""
     import numpy as np
@@ -427,7 +427,7 @@ def run_batched(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    bp = tp.config4()
+    bp = tp.problem_batched_banded()
     if world > 1:   # independent systems: each rank solves its share, no collective on the data path
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -490,7 +490,7 @@ def run_batched(args):
 
 
 def run_autograd(args):
-    """Configuration 5: loss = sum ||X - X_t||^2 with X = A^{-1} B through the differentiable
+    """Differentiable workload: loss = sum ||X - X_t||^2 with X = A^{-1} B through the differentiable
     solve (16 right-hand sides on the 512^2 convection-diffusion CSR system, FP64); a step is
     the forward multi-RHS solve plus the backward pass (transposed-matrix adjoint solve and
     the value gradient)."""
@@ -499,7 +499,7 @@ def run_autograd(args):
     import paper_1809_01948_gb300 as pb
     pb.build()
     dev = torch.device("cuda", 0)
-    mp = tp.config5()
+    mp = tp.problem_convdiff2d_multi()
     rp = torch.from_numpy(mp.A.row_ptr).to(dev)
     col = torch.from_numpy(mp.A.col).to(dev)
     vals0 = torch.from_numpy(mp.A.val).to(dev)
@@ -573,16 +573,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", action="store_true", help="measure the headline variant only")
     ap.add_argument("--grid", type=int, default=0, help="grid size per dimension (profiling of smaller cases)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
-                    help="c2: 2D convection-diffusion 1024^2 DIA (default); c3: 3D 256^3 CSR Neumann-2; "
-                         "c4: 512 batched systems; c5: differentiable solve, 16 RHS, forward + backward")
+    ap.add_argument("--workload", default="convdiff2d", choices=["convdiff2d", "convdiff3d", "batched", "autograd"],
+                    help="convdiff2d: 2D convection-diffusion 1024^2 DIA (default); convdiff3d: 3D 256^3 CSR "
+                         "Neumann-2; batched: 512 banded systems; autograd: differentiable solve, 16 RHS, "
+                         "forward + backward")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "c4":
+    elif args.workload == "batched":
         run_batched(args)
-    elif args.workload == "c5":
+    elif args.workload == "autograd":
         run_autograd(args)
     else:
         run_gpu(args)

@@ -198,9 +198,9 @@ extern "C" pbcg_status pbicgstab_solve_multi(pbcg_ctx* c, int32_t nrhs, const do
   }
   pbcg_status worst = PBCG_OK;
   if (res) {
-    for (int c2 = 0; c2 < nrhs; ++c2) {
-      res[c2].time_ms = ms_total;
-      if (res[c2].status != PBCG_OK && worst == PBCG_OK) worst = (pbcg_status)res[c2].status;
+    for (int j = 0; j < nrhs; ++j) {
+      res[j].time_ms = ms_total;
+      if (res[j].status != PBCG_OK && worst == PBCG_OK) worst = (pbcg_status)res[j].status;
     }
   }
   return worst;

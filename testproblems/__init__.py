@@ -27,6 +27,6 @@ from .problems import (  # noqa: F401
     CSR, Problem, BatchProblem, MultiProblem,
     stencil_2d, stencil_3d, csr_to_dia, normalise, csr_diag,
     poisson_2d, tp2, upwind_2d, upwind_3d,
-    config1, config2, config3, config4, config5,
+    problem_poisson2d, problem_convdiff2d, problem_convdiff3d, problem_batched_banded, problem_convdiff2d_multi,
     random_banded_system,
 )

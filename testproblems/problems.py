@@ -193,7 +193,7 @@ def upwind_3d(n: int, scale: float = 0.8) -> CSR:
                                     south=-1.0 - hb[1], north=-1.0, down=-1.0 - hb[2], up=-1.0))
 
 
-def config1(n: int = 100) -> Problem:
+def problem_poisson2d(n: int = 100) -> Problem:
     """2D Poisson 5-point, x* = 1/sqrt(N), b = A x*, x0 = 0, no preconditioner, tol 1e-12."""
     A, sigma = normalise(poisson_2d(n))
     N = A.n
@@ -202,7 +202,7 @@ def config1(n: int = 100) -> Problem:
                    precond="none", tol=1e-12, maxit=1000, fmt="csr", grid=(n, n), sigma=sigma)
 
 
-def config2(n: int = 1024, seed: int = 2) -> Problem:
+def problem_convdiff2d(n: int = 1024, seed: int = 2) -> Problem:
     """2D upwind convection-diffusion (cell Peclet 0.5), 5 diagonals, x* ~ U[0,1], Jacobi, tol 1e-10."""
     A, sigma = normalise(upwind_2d(n, 0.5))
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -211,7 +211,7 @@ def config2(n: int = 1024, seed: int = 2) -> Problem:
                    precond="jacobi", tol=1e-10, maxit=20000, fmt="dia", grid=(n, n), sigma=sigma)
 
 
-def config3(n: int = 256, seed: int = 3, degree: int = 2) -> Problem:
+def problem_convdiff3d(n: int = 256, seed: int = 3, degree: int = 2) -> Problem:
     """3D upwind convection-diffusion 7-point as CSR, x* ~ U[-1,1], Jacobi + Neumann(degree), tol 1e-10."""
     A, sigma = normalise(upwind_3d(n, 0.8))
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -273,7 +273,7 @@ def random_banded_system(N: int, rng: np.random.Generator, band: int = 256,
     return CSR(N, row_ptr.astype(np.int32), col, val)
 
 
-def config4(nsys: int = 512, seed: int = 4, n_lo: int = 2048, n_hi: int = 65536,
+def problem_batched_banded(nsys: int = 512, seed: int = 4, n_lo: int = 2048, n_hi: int = 65536,
             band: int = 256) -> BatchProblem:
     """Batched random banded systems, N_k ~ U{n_lo..n_hi}, FP32 values, x* ~ U[-1,1], b = A x* in FP64."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -288,7 +288,7 @@ def config4(nsys: int = 512, seed: int = 4, n_lo: int = 2048, n_hi: int = 65536,
     return BatchProblem("batched_%d" % nsys, systems, tol=1e-8, maxit=1000)
 
 
-def config5(n: int = 512, nrhs: int = 16, seed: int = 5) -> MultiProblem:
+def problem_convdiff2d_multi(n: int = 512, nrhs: int = 16, seed: int = 5) -> MultiProblem:
     """2D upwind convection-diffusion CSR FP64 with nrhs right-hand sides ~ N(0,1), targets ~ U[0,1]."""
     A, sigma = normalise(upwind_2d(n, 0.5))
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -14,7 +14,7 @@ import testproblems as tp  # noqa: E402
 from oracle import krylov  # noqa: E402
 
 if __name__ == "__main__":
-    p = tp.config2(1024)
+    p = tp.problem_convdiff2d(1024)
     A = p.A.to_scipy()
     out = {}
     for name, kw in [("fp64_rr100", dict(rr_period=100)), ("fp64_plain", dict())]:
@@ -23,5 +23,5 @@ if __name__ == "__main__":
         out[name] = dict(iterations=r.iterations, status=r.status.name, rel_res_true=r.rel_res_true,
                          n_replacements=r.n_replacements, seconds=round(time.time() - t, 1))
         print(name, out[name], flush=True)
-    out["workload"] = "convdiff2d_1024x1024, Jacobi, tol 1e-10, x0 = 0 (testproblems.config2(1024))"
+    out["workload"] = "convdiff2d_1024x1024, Jacobi, tol 1e-10, x0 = 0 (testproblems.problem_convdiff2d(1024))"
     json.dump(out, open(os.path.join(HERE, "oracle_iterations_convdiff2d_1024.json"), "w"), indent=1)

@@ -38,7 +38,7 @@ def _worker(rank, world, port, sizes, out):
 
 
 def test_two_gloo_ranks_split_batched_systems_and_take_max():
-    sizes = [int(s.A.n) for s in tp.config4(nsys=40, n_lo=100, n_hi=5000, band=32).systems]
+    sizes = [int(s.A.n) for s in tp.problem_batched_banded(nsys=40, n_lo=100, n_hi=5000, band=32).systems]
     port = _free_port()
     with mp.Manager() as m:
         out = m.dict()

@@ -20,7 +20,7 @@ def _csr_tensors(torch, A):
 def test_multi_rhs_matches_single_solves():
     torch = torch_cuda()
     import paper_1809_01948_gb300 as pb
-    m = tp.config5(n=48, nrhs=5)
+    m = tp.problem_convdiff2d_multi(n=48, nrhs=5)
     rp, col, val = _csr_tensors(torch, m.A)
     s = pb.Solver(m.A.n, row_ptr=rp, col=col, val=val, precond="jacobi", tol=1e-12, max_it=5000, rr_period=100)
     B = torch.from_numpy(m.B).cuda()
@@ -40,7 +40,7 @@ def test_multi_rhs_matches_single_solves():
 def test_more_rhs_than_teams_run_in_waves():
     torch = torch_cuda()
     import paper_1809_01948_gb300 as pb
-    m = tp.config5(n=16, nrhs=7)
+    m = tp.problem_convdiff2d_multi(n=16, nrhs=7)
     rp, col, val = _csr_tensors(torch, m.A)
     s = pb.Solver(m.A.n, row_ptr=rp, col=col, val=val, precond="jacobi", tol=1e-12, max_it=2000, rr_period=100,
                   grid_blocks=3)
@@ -55,7 +55,7 @@ def test_more_rhs_than_teams_run_in_waves():
 def test_transpose_context():
     torch = torch_cuda()
     import paper_1809_01948_gb300 as pb
-    m = tp.config5(n=40, nrhs=1)
+    m = tp.problem_convdiff2d_multi(n=40, nrhs=1)
     rp, col, val = _csr_tensors(torch, m.A)
     s = pb.Solver(m.A.n, row_ptr=rp, col=col, val=val, precond="jacobi", tol=1e-12, max_it=3000, rr_period=100)
     t = s.transpose()
@@ -73,7 +73,7 @@ def test_transpose_context():
 def test_value_grad_kernel_matches_oracle_formula():
     torch = torch_cuda()
     import paper_1809_01948_gb300 as pb
-    m = tp.config5(n=20, nrhs=3)
+    m = tp.problem_convdiff2d_multi(n=20, nrhs=3)
     rp, col, val = _csr_tensors(torch, m.A)
     s = pb.Solver(m.A.n, row_ptr=rp, col=col, val=val, precond="jacobi")
     rng = np.random.Generator(np.random.PCG64(4))
@@ -98,7 +98,7 @@ def _loss_and_grads(torch, pb, m, tol=1e-13):
 def test_autograd_matches_dense_adjoint():
     torch = torch_cuda()
     import paper_1809_01948_gb300 as pb
-    m = tp.config5(n=32, nrhs=16)
+    m = tp.problem_convdiff2d_multi(n=32, nrhs=16)
     X, gB, gv = _loss_and_grads(torch, pb, m)
     Xd, gBd, gvd = adjoint.dense_adjoint(m.A, m.B, m.X_target)
     assert np.linalg.norm(X - Xd) <= 1e-10 * np.linalg.norm(Xd)
@@ -189,7 +189,7 @@ def _fd_errors(torch, pb, m, n_entries, seed, tol, h_b, h_v):
 def test_autograd_matches_central_differences_small():
     torch = torch_cuda()
     import paper_1809_01948_gb300 as pb
-    eb, ev = _fd_check(torch, pb, tp.config5(n=40, nrhs=4), n_entries=12)
+    eb, ev = _fd_check(torch, pb, tp.problem_convdiff2d_multi(n=40, nrhs=4), n_entries=12)
     assert eb.max() <= 1e-6, eb
     assert ev.max() <= 1e-6, ev
 
@@ -204,7 +204,7 @@ def test_autograd_full_size_config5():
     is scaled: |fd - g| <= 1e-5 |g| + 1e-6 max|g| over the sampled entries."""
     torch = torch_cuda()
     import paper_1809_01948_gb300 as pb
-    m = tp.config5(n=512, nrhs=16)
+    m = tp.problem_convdiff2d_multi(n=512, nrhs=16)
     X, gB, gv, fb, fv = _fd_errors(torch, pb, m, n_entries=32, seed=5, tol=1e-12, h_b=1e-2, h_v=1e-4)
     A = m.A.to_scipy()
     AT = A.T.tocsr()

@@ -20,7 +20,7 @@ def _batch_solver(bp, **kw):
 
 
 def test_batched_small_uneven_matches_oracle():
-    bp = tp.config4(nsys=24, n_lo=50, n_hi=3000, band=64)
+    bp = tp.problem_batched_banded(nsys=24, n_lo=50, n_hi=3000, band=64)
     s, c, b = _batch_solver(bp, precision="mixed", tol=1e-8, max_it=500, rr_theta=1e-3)
     x, info = s.solve(b)
     x = x.cpu().numpy()
@@ -40,7 +40,7 @@ def test_batched_fp64_iterates_equal_single_solver():
     """FP64 batched solves give the same answers as the single-system solver."""
     torch = torch_cuda()
     from gpu_common import make_solver, gpu_solve
-    bp = tp.config4(nsys=5, n_lo=500, n_hi=2000, band=40)
+    bp = tp.problem_batched_banded(nsys=5, n_lo=500, n_hi=2000, band=40)
     s, c, b = _batch_solver(bp, precision="fp64", tol=1e-12, max_it=500, rr_period=50)
     x, info = s.solve(b)
     x = x.cpu().numpy()
@@ -55,7 +55,7 @@ def test_batched_fp64_iterates_equal_single_solver():
 
 
 def test_batched_graph_replay_and_autotune():
-    bp = tp.config4(nsys=40, n_lo=100, n_hi=5000, band=128)
+    bp = tp.problem_batched_banded(nsys=40, n_lo=100, n_hi=5000, band=128)
     s, c, b = _batch_solver(bp, precision="mixed", tol=1e-8, max_it=500, rr_theta=1e-3)
     x1, i1 = s.solve(b)
     x1 = x1.clone()
@@ -89,7 +89,7 @@ def test_batched_cluster_per_system_matches_single_solver(cluster):
     torch = torch_cuda()
     from gpu_common import make_solver, gpu_solve
     import paper_1809_01948_gb300 as pb
-    bp = tp.config4(nsys=12, n_lo=20, n_hi=6000, band=64)
+    bp = tp.problem_batched_banded(nsys=12, n_lo=20, n_hi=6000, band=64)
     c = bp.concat()
     dev = torch.device("cuda:0")
     s = pb.BatchSolver(c["row_off"], c["nnz_off"], torch.from_numpy(c["row_ptr"]).to(dev),
@@ -116,7 +116,7 @@ def test_batched_cluster_per_system_matches_single_solver(cluster):
 
 
 def test_batched_cluster_mixed_and_autotune_choice():
-    bp = tp.config4(nsys=30, n_lo=1000, n_hi=20000, band=128)
+    bp = tp.problem_batched_banded(nsys=30, n_lo=1000, n_hi=20000, band=128)
     s, c, b = _batch_solver(bp, precision="mixed", tol=1e-8, max_it=500, rr_theta=1e-3, cluster_blocks=4)
     x, info = s.solve(b)
     assert info["n_ok"] == 30 and info["cluster_blocks"] == 4
@@ -128,7 +128,7 @@ def test_batched_cluster_mixed_and_autotune_choice():
 def test_batched_cluster_option_rejected():
     torch = torch_cuda()
     import paper_1809_01948_gb300 as pb
-    bp = tp.config4(nsys=3, n_lo=100, n_hi=200, band=16)
+    bp = tp.problem_batched_banded(nsys=3, n_lo=100, n_hi=200, band=16)
     with pytest.raises(pb.PBCGError):
         _batch_solver(bp, cluster_blocks=3)
 
@@ -140,7 +140,7 @@ def test_batched_lanes_per_row_matches_single_solver(lanes, cluster):
     torch = torch_cuda()
     from gpu_common import make_solver, gpu_solve
     import paper_1809_01948_gb300 as pb
-    bp = tp.config4(nsys=10, n_lo=30, n_hi=5000, band=64)
+    bp = tp.problem_batched_banded(nsys=10, n_lo=30, n_hi=5000, band=64)
     c = bp.concat()
     dev = torch.device("cuda:0")
     s = pb.BatchSolver(c["row_off"], c["nnz_off"], torch.from_numpy(c["row_ptr"]).to(dev),

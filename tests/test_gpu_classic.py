@@ -10,10 +10,10 @@ from gpu_common import gpu_solve, make_solver, oracle_sensitivity, iterate_toler
 pytestmark = pytest.mark.gpu
 
 CASES = {
-    "poisson_100x100_jacobi_csr": (lambda: tp.config1(), "csr", "jacobi"),
-    "convdiff_128_jacobi_dia": (lambda: tp.config2(128), "dia", "jacobi"),
-    "convdiff_97_jacobi_csr_ragged": (lambda: tp.config2(97), "csr", "jacobi"),
-    "convdiff_64_none_dia": (lambda: tp.config2(64), "dia", "none"),
+    "poisson_100x100_jacobi_csr": (lambda: tp.problem_poisson2d(), "csr", "jacobi"),
+    "convdiff_128_jacobi_dia": (lambda: tp.problem_convdiff2d(128), "dia", "jacobi"),
+    "convdiff_97_jacobi_csr_ragged": (lambda: tp.problem_convdiff2d(97), "csr", "jacobi"),
+    "convdiff_64_none_dia": (lambda: tp.problem_convdiff2d(64), "dia", "none"),
 }
 
 
@@ -65,7 +65,7 @@ def test_classic_final_true_residual(name):
 def test_classic_and_pipelined_reach_the_same_solution():
     """Algorithms 1 and 2 are the same method in exact arithmetic (Section 2): on a
     well-conditioned problem both converge, to the same x up to the tolerance."""
-    prob = tp.config2(100)
+    prob = tp.problem_convdiff2d(100)
     A = prob.A.to_scipy()
     xd = np.linalg.solve(A.toarray(), prob.b)
     sc = classic_solver(prob, "dia", "jacobi", tol=1e-10, max_it=3000)
@@ -80,7 +80,7 @@ def test_classic_and_pipelined_reach_the_same_solution():
 
 def test_classic_edge_cases():
     # b = 0 gives x = 0 without an iteration
-    prob = tp.config2(20)
+    prob = tp.problem_convdiff2d(20)
     s = classic_solver(prob, "dia", "jacobi", tol=1e-10, max_it=100)
     x, res, _, _ = gpu_solve(s, np.zeros(prob.A.n), x0=np.ones(prob.A.n))
     assert res.status == 0 and res.iterations == 0 and np.all(x == 0)
@@ -116,7 +116,7 @@ def test_classic_breakdown_matches_oracle():
 
 
 def test_classic_deterministic_and_launch_shapes():
-    prob = tp.config2(80)
+    prob = tp.problem_convdiff2d(80)
     A = prob.A.to_scipy()
     s = classic_solver(prob, "dia", "jacobi", tol=1e-10, max_it=3000)
     x1, r1, _, _ = gpu_solve(s, prob.b)
@@ -132,13 +132,13 @@ def test_classic_deterministic_and_launch_shapes():
 def test_classic_option_rejections():
     torch = torch_cuda()
     import paper_1809_01948_gb300 as pb
-    prob = tp.config2(16)
+    prob = tp.problem_convdiff2d(16)
     for kw in (dict(precision="mixed"), dict(rr_period=10), dict(rr_theta=1e-3), dict(rr_auto=True),
                dict(max_restarts=1)):
         with pytest.raises(pb.PBCGError) as e:
             classic_solver(prob, "dia", "jacobi", **kw)
         assert e.value.status == 1, kw
-    p3 = tp.config3(8)
+    p3 = tp.problem_convdiff3d(8)
     with pytest.raises(pb.PBCGError):
         make_solver(p3, fmt="csr", method="classic")          # Neumann preconditioner
     s = make_solver(p3, fmt="csr")

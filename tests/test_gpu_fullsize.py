@@ -25,26 +25,26 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 @pytest.fixture(scope="module")
-def c2():
-    return tp.config2(1024)
+def convdiff2d():
+    return tp.problem_convdiff2d(1024)
 
 
 @pytest.fixture(scope="module")
-def c3():
-    return tp.config3(256)
+def convdiff3d():
+    return tp.problem_convdiff3d(256)
 
 
 def _true_rel(A, b, x):
     return float(np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b))
 
 
-def test_convdiff2d_1024_first_iterates(c2):
+def test_convdiff2d_1024_first_iterates(convdiff2d):
     K = 8
-    A = c2.A.to_scipy()
-    ref, sens = oracle_sensitivity(A, c2.b, K, precond="jacobi", rr_period=100)
+    A = convdiff2d.A.to_scipy()
+    ref, sens = oracle_sensitivity(A, convdiff2d.b, K, precond="jacobi", rr_period=100)
     tol_i = iterate_tolerance(sens)
-    s = make_solver(c2, fmt="dia", tol=1e-300, max_it=K, rr_period=100)
-    _, res, its, hist = gpu_solve(s, c2.b, K=K, hist_len=K)
+    s = make_solver(convdiff2d, fmt="dia", tol=1e-300, max_it=K, rr_period=100)
+    _, res, its, hist = gpu_solve(s, convdiff2d.b, K=K, hist_len=K)
     assert res.iterations == K
     for i in range(K):
         d = np.linalg.norm(its[i] - ref.xs[i]) / np.linalg.norm(ref.xs[i])
@@ -54,14 +54,14 @@ def test_convdiff2d_1024_first_iterates(c2):
 
 
 @pytest.mark.parametrize("method", ["pipelined", "classic"])
-def test_convdiff2d_1024_full_solve(c2, method):
+def test_convdiff2d_1024_full_solve(convdiff2d, method):
     golden = json.load(open(os.path.join(HERE, "golden", "oracle_iterations_convdiff2d_1024.json")))["fp64_rr100"]
-    A = c2.A.to_scipy()
+    A = convdiff2d.A.to_scipy()
     kw = dict(rr_period=100) if method == "pipelined" else {}
-    s = make_solver(c2, fmt="dia", tol=1e-10, max_it=20000, method=method, **kw)
-    x, res, _, _ = gpu_solve(s, c2.b)
+    s = make_solver(convdiff2d, fmt="dia", tol=1e-10, max_it=20000, method=method, **kw)
+    x, res, _, _ = gpu_solve(s, convdiff2d.b)
     assert res.status == 0, res.as_dict()
-    true = _true_rel(A, c2.b, x)
+    true = _true_rel(A, convdiff2d.b, x)
     assert true <= 1e-10
     assert abs(true - res.rel_res_true) <= 1e-3 * true
     if method == "pipelined":
@@ -71,15 +71,15 @@ def test_convdiff2d_1024_full_solve(c2, method):
         assert res.n_replacements >= 1
 
 
-def test_convdiff3d_256_first_iterates(c3):
+def test_convdiff3d_256_first_iterates(convdiff3d):
     """Three iterations of Algorithm 2 with Neumann(2) at 16.7M rows.  On this operator the
     oracle's self-sensitivity is below 1e-14 at iterate 3 (8e-13 at iterate 20 on 24^3), so
     the 1e-10 floor of the iterate tolerance applies."""
     K = 3
-    A = c3.A.to_scipy()
-    ref = oracle.pbicgstab(A, c3.b, precond="neumann", degree=2, tol=1e-300, maxit=K, record=K, rr_period=100)
-    s = make_solver(c3, fmt="csr", tol=1e-300, max_it=K, rr_period=100)
-    _, res, its, hist = gpu_solve(s, c3.b, K=K, hist_len=K)
+    A = convdiff3d.A.to_scipy()
+    ref = oracle.pbicgstab(A, convdiff3d.b, precond="neumann", degree=2, tol=1e-300, maxit=K, record=K, rr_period=100)
+    s = make_solver(convdiff3d, fmt="csr", tol=1e-300, max_it=K, rr_period=100)
+    _, res, its, hist = gpu_solve(s, convdiff3d.b, K=K, hist_len=K)
     assert res.iterations == K
     for i in range(K):
         d = np.linalg.norm(its[i] - ref.xs[i]) / np.linalg.norm(ref.xs[i])
@@ -89,28 +89,28 @@ def test_convdiff3d_256_first_iterates(c3):
 
 
 @pytest.mark.parametrize("precision,kw", [("fp64", dict(rr_period=100)), ("mixed", dict(rr_theta=3e-3))])
-def test_convdiff3d_256_full_solve(c3, precision, kw):
-    A = c3.A.to_scipy()
-    s = make_solver(c3, fmt="csr", precision=precision, tol=1e-10, max_it=2000, **kw)
-    x, res, _, _ = gpu_solve(s, c3.b)
+def test_convdiff3d_256_full_solve(convdiff3d, precision, kw):
+    A = convdiff3d.A.to_scipy()
+    s = make_solver(convdiff3d, fmt="csr", precision=precision, tol=1e-10, max_it=2000, **kw)
+    x, res, _, _ = gpu_solve(s, convdiff3d.b)
     assert res.status == 0, res.as_dict()
-    true = _true_rel(A, c3.b, x)
+    true = _true_rel(A, convdiff3d.b, x)
     assert true <= 1e-10
     assert abs(true - res.rel_res_true) <= 1e-3 * true
     assert 150 <= res.iterations <= 600, res.iterations
 
 
-def test_convdiff2d_1024_automated_replacement_schedule(c2):
+def test_convdiff2d_1024_automated_replacement_schedule(convdiff2d):
     """Eq. (criterion) at full size: over the first 150 iterations the GPU replaces in the
     same iterations as the oracle (both compute the bound f^r of Eq. DDr_bound from the same
     norms and constants).  On this system the criterion fires every 6-15 iterations from the
     start and the solve eventually diverges, in the oracle as on the GPU (the design notes
     record it); only the schedule is compared here."""
     K = 150
-    A = c2.A.to_scipy()
-    ref = oracle.pbicgstab(A, c2.b, precond="jacobi", tol=1e-300, maxit=K, rr_auto=True)
-    s = make_solver(c2, fmt="dia", tol=1e-300, max_it=K, rr_auto=True)
-    _, res, _, hist = gpu_solve(s, c2.b, hist_len=K)
+    A = convdiff2d.A.to_scipy()
+    ref = oracle.pbicgstab(A, convdiff2d.b, precond="jacobi", tol=1e-300, maxit=K, rr_auto=True)
+    s = make_solver(convdiff2d, fmt="dia", tol=1e-300, max_it=K, rr_auto=True)
+    _, res, _, hist = gpu_solve(s, convdiff2d.b, hist_len=K)
     rep_gpu = [i for i in range(res.iterations) if hist[i, 4] == 1.0]
     rep_ref = [i for i, f in enumerate(ref.replaced) if f]
     assert len(rep_ref) >= 8

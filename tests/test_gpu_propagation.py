@@ -53,7 +53,7 @@ def test_random_scalars_match_oracle(m):
 def test_convection_diffusion_run_matches_oracle():
     """The scalars of 300 iterations of the oracle's Algorithm 2 on the 2D convection-diffusion
     problem (64 x 64, Jacobi), where the products grow by orders of magnitude."""
-    p = tp.config2(64)
+    p = tp.problem_convdiff2d(64)
     res = oracle.pbicgstab(p.A.to_scipy(), p.b, precond="jacobi", tol=1e-30, maxit=301)
     al, om, be = np.array(res.alpha[:300]), np.array(res.omega[:300]), np.array(res.beta[:300])
     ref = pg.propagation_column_norms(al, be, om)

@@ -14,11 +14,11 @@ pytestmark = pytest.mark.gpu
 def test_spmv_matches_oracle(which):
     torch = torch_cuda()
     if which == "poisson_csr":
-        prob, fmt = tp.config1(37), "csr"
+        prob, fmt = tp.problem_poisson2d(37), "csr"
     elif which == "upwind_dia":
-        prob, fmt = tp.config2(45), "dia"
+        prob, fmt = tp.problem_convdiff2d(45), "dia"
     elif which == "upwind3d_csr":
-        prob, fmt = tp.config3(13), "csr"
+        prob, fmt = tp.problem_convdiff3d(13), "csr"
     else:
         rng = np.random.Generator(np.random.PCG64(9))
         A = tp.random_banded_system(5000, rng)
@@ -34,10 +34,10 @@ def test_spmv_matches_oracle(which):
 
 # ------------------------------------------------------------------ FP64 iterates
 CASES = {
-    "config1_poisson_100x100": (lambda: tp.config1(), "csr", {}),
-    "config2_convdiff_128_dia": (lambda: tp.config2(128), "dia", dict(rr_period=100)),
-    "config2_convdiff_97_csr_ragged": (lambda: tp.config2(97), "csr", dict(rr_period=100)),
-    "config3_convdiff3d_24_neumann2": (lambda: tp.config3(24), "csr", dict(rr_period=100)),
+    "config1_poisson_100x100": (lambda: tp.problem_poisson2d(), "csr", {}),
+    "config2_convdiff_128_dia": (lambda: tp.problem_convdiff2d(128), "dia", dict(rr_period=100)),
+    "config2_convdiff_97_csr_ragged": (lambda: tp.problem_convdiff2d(97), "csr", dict(rr_period=100)),
+    "config3_convdiff3d_24_neumann2": (lambda: tp.problem_convdiff3d(24), "csr", dict(rr_period=100)),
 }
 
 
@@ -86,7 +86,7 @@ def test_fp64_final_true_residual(name):
 
 
 def test_replacement_schedule_matches_oracle():
-    prob = tp.config2(64)
+    prob = tp.problem_convdiff2d(64)
     A = prob.A.to_scipy()
     ref = oracle.pbicgstab(A, prob.b, precond="jacobi", tol=1e-12, maxit=400, rr_period=25)
     s = make_solver(prob, fmt="dia", tol=1e-12, max_it=400, rr_period=25)
@@ -100,7 +100,7 @@ def test_replacement_schedule_matches_oracle():
 
 # ------------------------------------------------------------------ mixed precision
 def test_mixed_first_iterates_track_oracle_emulation():
-    prob = tp.config2(64)
+    prob = tp.problem_convdiff2d(64)
     A = prob.A.to_scipy()
     K = 6
     ref = oracle.pbicgstab(A, prob.b, precond="jacobi", tol=1e-300, maxit=K, record=K, mixed=True)
@@ -112,7 +112,7 @@ def test_mixed_first_iterates_track_oracle_emulation():
 
 
 def test_mixed_reaches_tolerance_with_replacement():
-    prob = tp.config2(64)
+    prob = tp.problem_convdiff2d(64)
     A = prob.A.to_scipy()
     s = make_solver(prob, precision="mixed", fmt="dia", tol=1e-10, max_it=3000, rr_theta=1e-3)
     x, res, _, _ = gpu_solve(s, prob.b)
@@ -124,14 +124,14 @@ def test_mixed_reaches_tolerance_with_replacement():
 
 # ------------------------------------------------------------------ edge cases
 def test_zero_rhs_gives_zero():
-    prob = tp.config2(20)
+    prob = tp.problem_convdiff2d(20)
     s = make_solver(prob, fmt="dia", tol=1e-10, max_it=100)
     x, res, _, _ = gpu_solve(s, np.zeros(prob.A.n), x0=np.ones(prob.A.n))
     assert res.status == 0 and res.iterations == 0 and np.all(x == 0)
 
 
 def test_exact_initial_guess():
-    prob = tp.config2(20)
+    prob = tp.problem_convdiff2d(20)
     xd = np.linalg.solve(prob.A.to_scipy().toarray(), prob.b)
     s = make_solver(prob, fmt="dia", tol=1e-10, max_it=100)
     x, res, _, _ = gpu_solve(s, prob.b, x0=xd)
@@ -150,7 +150,7 @@ def test_single_row_and_tiny_systems():
 
 
 def test_max_it_zero_and_not_converged():
-    prob = tp.config2(32)
+    prob = tp.problem_convdiff2d(32)
     s = make_solver(prob, fmt="dia", tol=1e-10, max_it=0)
     _, res, _, _ = gpu_solve(s, prob.b)
     assert res.status == 4 and res.iterations == 0
@@ -192,7 +192,7 @@ def test_invalid_matrix_rejected():
 
 
 def test_deterministic_bitwise():
-    prob = tp.config2(100)
+    prob = tp.problem_convdiff2d(100)
     s = make_solver(prob, fmt="dia", tol=1e-10, max_it=3000, rr_period=100)
     x1, r1, _, _ = gpu_solve(s, prob.b)
     x2, r2, _, _ = gpu_solve(s, prob.b)
@@ -201,7 +201,7 @@ def test_deterministic_bitwise():
 
 def test_launch_shapes_agree():
     """Different grid sizes change only the reduction order (rounding level)."""
-    prob = tp.config2(80)
+    prob = tp.problem_convdiff2d(80)
     A = prob.A.to_scipy()
     out = []
     for grid, threads in ((1, 256), (7, 128), (0, 0), (150, 1024)):
@@ -222,14 +222,14 @@ def test_barrier_timeout_is_reported_not_hung():
     assert st == "TIMEOUT"
     assert time.time() - t < 10.0
     # the context is still usable afterwards
-    prob = tp.config2(16)
+    prob = tp.problem_convdiff2d(16)
     s = make_solver(prob, fmt="dia", tol=1e-10, max_it=500)
     _, res, _, _ = gpu_solve(s, prob.b)
     assert res.status == 0
 
 
 def test_host_buffers_end_to_end():
-    prob = tp.config2(40)
+    prob = tp.problem_convdiff2d(40)
     s = make_solver(prob, fmt="dia", tol=1e-10, max_it=2000, rr_period=100)
     x = np.zeros(prob.A.n)
     x, res = s.solve_host(prob.b, x)
@@ -238,9 +238,9 @@ def test_host_buffers_end_to_end():
 
 
 # ------------------------------------------------------------------ automated replacement
-@pytest.mark.parametrize("name,maker,fmt,tol", [("convdiff2d_64_dia", lambda: tp.config2(64), "dia", 1e-12),
-                                                 ("convdiff2d_64_csr", lambda: tp.config2(64), "csr", 1e-12),
-                                                 ("poisson2d_100_csr", lambda: tp.config1(), "csr", 1e-10)])
+@pytest.mark.parametrize("name,maker,fmt,tol", [("convdiff2d_64_dia", lambda: tp.problem_convdiff2d(64), "dia", 1e-12),
+                                                 ("convdiff2d_64_csr", lambda: tp.problem_convdiff2d(64), "csr", 1e-12),
+                                                 ("poisson2d_100_csr", lambda: tp.problem_poisson2d(), "csr", 1e-10)])
 def test_automated_replacement_schedule_matches_oracle(name, maker, fmt, tol):
     """Eq. (criterion) with the run-time bound f^r of Eq. (DDr_bound): the GPU replaces in the
     same iterations as the oracle (the bound's constants and norms agree to rounding)."""
@@ -268,6 +268,6 @@ def test_automated_replacement_schedule_matches_oracle(name, maker, fmt, tol):
 def test_automated_replacement_rejected_with_neumann():
     torch_cuda()
     import paper_1809_01948_gb300 as pb
-    prob = tp.config3(8)
+    prob = tp.problem_convdiff3d(8)
     with pytest.raises(pb.PBCGError):
         make_solver(prob, rr_auto=True)

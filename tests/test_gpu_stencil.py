@@ -26,15 +26,15 @@ def _variable_coefficients(prob, seed=3):
 
 def test_detection():
     torch_cuda()
-    assert make_solver(tp.config1(30), fmt="csr", precond="none").storage == "stencil"
-    assert make_solver(tp.config2(40), fmt="dia").storage == "stencil"
-    assert make_solver(tp.config2(40), fmt="csr").storage == "stencil"
-    assert make_solver(tp.config3(10), fmt="csr").storage == "stencil"
+    assert make_solver(tp.problem_poisson2d(30), fmt="csr", precond="none").storage == "stencil"
+    assert make_solver(tp.problem_convdiff2d(40), fmt="dia").storage == "stencil"
+    assert make_solver(tp.problem_convdiff2d(40), fmt="csr").storage == "stencil"
+    assert make_solver(tp.problem_convdiff3d(10), fmt="csr").storage == "stencil"
     T2 = tp.tp2(20)
     p2 = tp.Problem("tp2", T2, np.ones(T2.n), np.zeros(T2.n), None, precond="jacobi", fmt="csr")
     assert make_solver(p2).storage == "stencil"
-    assert make_solver(tp.config2(40), fmt="dia", operator_storage="general").storage == "general"
-    var = _variable_coefficients(tp.config2(40))
+    assert make_solver(tp.problem_convdiff2d(40), fmt="dia", operator_storage="general").storage == "general"
+    var = _variable_coefficients(tp.problem_convdiff2d(40))
     assert make_solver(var, fmt="csr").storage == "general"
     assert make_solver(var, fmt="dia").storage == "general"
     rng = np.random.Generator(np.random.PCG64(9))
@@ -44,13 +44,13 @@ def test_detection():
 
 
 CASES = {
-    "poisson_csr_none": (lambda: tp.config1(60), "csr", "fp64", "pipelined", dict()),
-    "convdiff2d_dia_jacobi": (lambda: tp.config2(96), "dia", "fp64", "pipelined", dict(rr_period=50)),
-    "convdiff2d_csr_jacobi_mixed": (lambda: tp.config2(64), "csr", "mixed", "pipelined", dict(rr_theta=1e-3)),
-    "convdiff3d_csr_neumann": (lambda: tp.config3(20), "csr", "fp64", "pipelined", dict(rr_period=50)),
-    "convdiff3d_csr_neumann_mixed": (lambda: tp.config3(20), "csr", "mixed", "pipelined", dict(rr_theta=3e-3)),
-    "convdiff2d_dia_classic": (lambda: tp.config2(96), "dia", "fp64", "classic", dict()),
-    "convdiff2d_dia_auto_rr": (lambda: tp.config2(64), "dia", "fp64", "pipelined", dict(rr_auto=True)),
+    "poisson_csr_none": (lambda: tp.problem_poisson2d(60), "csr", "fp64", "pipelined", dict()),
+    "convdiff2d_dia_jacobi": (lambda: tp.problem_convdiff2d(96), "dia", "fp64", "pipelined", dict(rr_period=50)),
+    "convdiff2d_csr_jacobi_mixed": (lambda: tp.problem_convdiff2d(64), "csr", "mixed", "pipelined", dict(rr_theta=1e-3)),
+    "convdiff3d_csr_neumann": (lambda: tp.problem_convdiff3d(20), "csr", "fp64", "pipelined", dict(rr_period=50)),
+    "convdiff3d_csr_neumann_mixed": (lambda: tp.problem_convdiff3d(20), "csr", "mixed", "pipelined", dict(rr_theta=3e-3)),
+    "convdiff2d_dia_classic": (lambda: tp.problem_convdiff2d(96), "dia", "fp64", "classic", dict()),
+    "convdiff2d_dia_auto_rr": (lambda: tp.problem_convdiff2d(64), "dia", "fp64", "pipelined", dict(rr_auto=True)),
 }
 
 
@@ -75,7 +75,7 @@ def test_solves_bitwise_equal_to_general_storage(name):
 @pytest.mark.parametrize("fmt", ["csr", "dia"])
 def test_spmv_and_true_residual_equal(fmt):
     torch = torch_cuda()
-    prob = tp.config2(50)
+    prob = tp.problem_convdiff2d(50)
     sa = make_solver(prob, fmt=fmt)
     sg = make_solver(prob, fmt=fmt, operator_storage="general")
     rng = np.random.Generator(np.random.PCG64(4))
@@ -88,6 +88,6 @@ def test_spmv_and_true_residual_equal(fmt):
 def test_storage_fixed_at_create():
     torch_cuda()
     import paper_1809_01948_gb300 as pb
-    s = make_solver(tp.config2(20), fmt="dia")
+    s = make_solver(tp.problem_convdiff2d(20), fmt="dia")
     with pytest.raises(pb.PBCGError):
         s.set_options(operator_storage="general")

@@ -6,7 +6,7 @@ import testproblems as tp
 
 
 def test_dense_adjoint_matches_central_differences():
-    m = tp.config5(n=5, nrhs=3)
+    m = tp.problem_convdiff2d_multi(n=5, nrhs=3)
     A = m.A
     X, gb, gv = adjoint.dense_adjoint(A, m.B, m.X_target)
     Ad = A.to_scipy().toarray()
@@ -35,7 +35,7 @@ def test_dense_adjoint_matches_central_differences():
 
 
 def test_sparse_adjoint_matches_dense():
-    m = tp.config5(n=12, nrhs=2)
+    m = tp.problem_convdiff2d_multi(n=12, nrhs=2)
     Xd, gbd, gvd = adjoint.dense_adjoint(m.A, m.B, m.X_target)
     Xs, gbs, gvs = adjoint.sparse_adjoint(m.A, m.B, m.X_target, tol=1e-13)
     assert np.linalg.norm(Xs - Xd) <= 1e-11 * np.linalg.norm(Xd)

@@ -18,12 +18,12 @@ def _scipy_iterates(A, b, nit, M=None):
 def test_classic_matches_scipy_iterates(which):
     """scipy's bicgstab uses the same shadow vector r_0 and right preconditioning."""
     if which == "poisson":
-        p = tp.config1(30)
+        p = tp.problem_poisson2d(30)
         A = p.A.to_scipy()
         M = None
         prec = "none"
     else:
-        p = tp.config2(24)
+        p = tp.problem_convdiff2d(24)
         A = p.A.to_scipy()
         dinv = 1.0 / A.diagonal()
         M = spl.LinearOperator(A.shape, matvec=lambda v: dinv * v)
@@ -35,7 +35,7 @@ def test_classic_matches_scipy_iterates(which):
 
 
 def test_classic_converges_to_dense_lu():
-    p = tp.config2(15)
+    p = tp.problem_convdiff2d(15)
     A = p.A.to_scipy()
     res = oracle.bicgstab(A, p.b, precond="jacobi", tol=1e-13, maxit=500)
     xd = np.linalg.solve(A.toarray(), p.b)

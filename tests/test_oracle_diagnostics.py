@@ -16,10 +16,10 @@ CASES = [("poisson", "none", 0), ("upwind", "jacobi", 0), ("upwind3d", "neumann"
 
 def _problem(which):
     if which == "poisson":
-        return tp.config1(40)
+        return tp.problem_poisson2d(40)
     if which == "upwind":
-        return tp.config2(40)
-    return tp.config3(10)
+        return tp.problem_convdiff2d(40)
+    return tp.problem_convdiff3d(10)
 
 
 def _probe_run(which, prec, deg, maxit=40, **kw):
@@ -79,7 +79,7 @@ def test_gap_bound_resets_at_replacement():
 @pytest.mark.parametrize("prec", ["none", "jacobi"])
 def test_classic_gap_is_superposition(prec):
     """Eq. (classic_nomatrix): Delta^r_i = Delta^r_0 - sum_j (A dx_j + dr_j + dq_j)."""
-    p = tp.config2(30)
+    p = tp.problem_convdiff2d(30)
     A = p.A.to_scipy()
     M = oracle.make_precond(prec, A)
     probe = diagnostics.ClassicProbe(A, p.b, None, prec, M.dinv, 0)

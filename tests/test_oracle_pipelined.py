@@ -16,7 +16,7 @@ def test_pipelined_equals_classic_config1_first_20():
     """Section 1 / Section 3: Algorithm 2 produces the iterates of Algorithm 1 in exact
     arithmetic; in FP64 they agree to <= 1e-10 relative over the first 20 iterations
     (2D Poisson 100x100, N = 10,000, x* = 1/sqrt(N), x0 = 0, no preconditioner)."""
-    p = tp.config1()
+    p = tp.problem_poisson2d()
     A = p.A.to_scipy()
     c = oracle.bicgstab(A, p.b, tol=p.tol, maxit=20, record=20)
     q = oracle.pbicgstab(A, p.b, tol=p.tol, maxit=20, record=20)
@@ -26,9 +26,9 @@ def test_pipelined_equals_classic_config1_first_20():
     assert np.allclose(c.omega[:20], q.omega[:20], rtol=1e-9)
 
 
-@pytest.mark.parametrize("prec,deg,maker", [("jacobi", 0, lambda: tp.config2(48)),
-                                            ("neumann", 2, lambda: tp.config3(10)),
-                                            ("neumann", 1, lambda: tp.config2(32))])
+@pytest.mark.parametrize("prec,deg,maker", [("jacobi", 0, lambda: tp.problem_convdiff2d(48)),
+                                            ("neumann", 2, lambda: tp.problem_convdiff3d(10)),
+                                            ("neumann", 1, lambda: tp.problem_convdiff2d(32))])
 def test_pipelined_equals_classic_preconditioned(prec, deg, maker):
     """Preconditioned equivalence.  On the convection-diffusion operators the FP64 drift
     between the two algorithms reaches 1e-10 around iteration 15 (a near-cancellation in
@@ -41,9 +41,9 @@ def test_pipelined_equals_classic_preconditioned(prec, deg, maker):
 
 
 def test_config1_outcomes():
-    """Config 1: classic reaches 1e-12; plain p-BiCGStab stops with its recursive residual
+    """Poisson 100x100, no preconditioner: classic reaches 1e-12; plain p-BiCGStab stops with its recursive residual
     below 1e-12 (and a true residual within 10x of it, reading R5)."""
-    p = tp.config1()
+    p = tp.problem_poisson2d()
     A = p.A.to_scipy()
     c = oracle.bicgstab(A, p.b, tol=1e-12, maxit=1000)
     q = oracle.pbicgstab(A, p.b, tol=1e-12, maxit=1000)
@@ -57,7 +57,7 @@ def test_config1_outcomes():
 
 @pytest.mark.parametrize("prec,deg", [("none", 0), ("jacobi", 0), ("neumann", 2)])
 def test_pipelined_converges_to_dense_lu(prec, deg):
-    p = tp.config2(14)
+    p = tp.problem_convdiff2d(14)
     A = p.A.to_scipy()
     res = oracle.pbicgstab(A, p.b, precond=prec, degree=deg, tol=1e-12, maxit=1000, rr_period=50)
     xd = np.linalg.solve(A.toarray(), p.b)
@@ -69,7 +69,7 @@ def test_pipelined_converges_to_dense_lu(prec, deg):
 def test_jacobi_scale_invariance_constant_diagonal():
     """With a constant diagonal, D^{-1} = c I, and the Krylov iterates do not depend on c:
     Jacobi-preconditioned iterates equal the unpreconditioned ones."""
-    p = tp.config2(40)
+    p = tp.problem_convdiff2d(40)
     A = p.A.to_scipy()
     assert np.all(A.diagonal() == A.diagonal()[0])
     a = oracle.pbicgstab(A, p.b, precond="none", tol=1e-30, maxit=20, record=20)
@@ -79,7 +79,7 @@ def test_jacobi_scale_invariance_constant_diagonal():
 
 def test_neumann_matches_explicit_polynomial():
     """M^{-1} = sum_{j=0..d} (I - D^{-1} A)^j D^{-1} (dense closed form) vs the Horner recursion."""
-    p = tp.config2(6)
+    p = tp.problem_convdiff2d(6)
     A = p.A.to_scipy()
     Ad = A.toarray()
     Dinv = np.diag(1.0 / np.diag(Ad))
@@ -96,7 +96,7 @@ def test_neumann_matches_explicit_polynomial():
 
 
 def test_zero_rhs_and_exact_start():
-    p = tp.config2(8)
+    p = tp.problem_convdiff2d(8)
     A = p.A.to_scipy()
     r = oracle.pbicgstab(A, np.zeros(A.shape[0]), precond="jacobi")
     assert r.status == oracle.Status.OK and r.iterations == 0 and np.all(r.x == 0)
@@ -114,13 +114,13 @@ def test_breakdown_detected():
 
 
 def test_maxit_not_converged():
-    p = tp.config2(32)
+    p = tp.problem_convdiff2d(32)
     r = oracle.pbicgstab(p.A.to_scipy(), p.b, precond="jacobi", tol=1e-10, maxit=5)
     assert r.status == oracle.Status.NOT_CONVERGED and r.iterations == 5
 
 
 def test_record_and_history_lengths():
-    p = tp.config2(16)
+    p = tp.problem_convdiff2d(16)
     r = oracle.pbicgstab(p.A.to_scipy(), p.b, precond="jacobi", tol=1e-10, maxit=200, record=7)
     assert len(r.xs) == 7 and len(r.alpha) == r.iterations and len(r.rnorm) == r.iterations
     assert np.isclose(r.rnorm[-1] / np.linalg.norm(p.b), r.rel_res_recursive)

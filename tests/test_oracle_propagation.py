@@ -21,7 +21,7 @@ CASES = [("poisson", "none"), ("upwind", "jacobi")]
 
 
 def _run(which, prec, K):
-    p = tp.config1(16) if which == "poisson" else tp.config2(16)
+    p = tp.problem_poisson2d(16) if which == "poisson" else tp.problem_convdiff2d(16)
     A = p.A.to_scipy()
     M = oracle.make_precond(prec, A, 0)
     probe = diagnostics.PipelinedProbe(A, p.b, prec, M.dinv, 0, M, keep_vectors=True)
@@ -163,7 +163,7 @@ def test_growth_on_a_real_run_is_reported_per_column():
     """On the convection-diffusion run the products grow by orders of magnitude (the
     paper's observation), and column j depends on the first j iterations only (up to the
     rounding of differently blocked dense products)."""
-    p = tp.config2(64)
+    p = tp.problem_convdiff2d(64)
     res = oracle.pbicgstab(p.A.to_scipy(), p.b, precond="jacobi", tol=1e-30, maxit=120)
     al, om, be = np.array(res.alpha), np.array(res.omega), np.array(res.beta)
     N = pg.propagation_column_norms(al[:119], be[:119], om[:119])

@@ -9,7 +9,7 @@ import testproblems as tp
 
 def test_periodic_schedule_and_cutoff():
     """Reading R7: replacements in iterations P, 2P, ... while ||r_i|| >= sqrt(eps) ||r_0||."""
-    p = tp.config2(48)
+    p = tp.problem_convdiff2d(48)
     A = p.A.to_scipy()
     r = oracle.pbicgstab(A, p.b, precond="jacobi", tol=1e-13, maxit=400, rr_period=25)
     rep = [i for i, f in enumerate(r.replaced) if f]
@@ -24,7 +24,7 @@ def test_periodic_schedule_and_cutoff():
 def test_replacement_resets_recursive_residual():
     """Right after Eq. (rr) the recursive residual equals b - A x up to the round-off of
     one FP64 SpMV: the logged ||r_{i+1}|| matches the true residual of x_{i+1}."""
-    p = tp.config2(40)
+    p = tp.problem_convdiff2d(40)
     A = p.A.to_scipy()
     seen = []
 
@@ -38,7 +38,7 @@ def test_replacement_resets_recursive_residual():
 def test_replacement_improves_attainable_accuracy():
     """Section 4.3 / Fig. 'unsymmetric': without replacement p-BiCGStab stagnates above
     the accuracy classic BiCGStab attains; with replacements it reaches the classic level."""
-    p = tp.config2(64)
+    p = tp.problem_convdiff2d(64)
     A = p.A.to_scipy()
     plain = oracle.pbicgstab(A, p.b, precond="jacobi", tol=1e-12, maxit=2000)
     rr = oracle.pbicgstab(A, p.b, precond="jacobi", tol=1e-12, maxit=2000, rr_period=100)
@@ -50,7 +50,7 @@ def test_automated_replacement_reaches_tolerance():
     """Eq. (criterion) with tau = sqrt(eps): replacements happen, tolerance reached where
     plain p-BiCGStab stagnates (the bound f^r built from the paper's worst-case local
     error bounds is loose, so the count is larger than with a periodic policy)."""
-    p = tp.config2(64)
+    p = tp.problem_convdiff2d(64)
     A = p.A.to_scipy()
     r = oracle.pbicgstab(A, p.b, precond="jacobi", tol=1e-12, maxit=2000, rr_auto=True)
     assert r.status == oracle.Status.OK and r.rel_res_true <= 1e-12
@@ -60,7 +60,7 @@ def test_automated_replacement_reaches_tolerance():
 
 def test_mixed_first_iterates_track_fp64():
     """Mixed emulation: the first iterates agree with FP64 to FP32 accuracy."""
-    p = tp.config2(64)
+    p = tp.problem_convdiff2d(64)
     A = p.A.to_scipy()
     f = oracle.pbicgstab(A, p.b, precond="jacobi", tol=1e-30, maxit=5, record=5)
     m = oracle.pbicgstab(A, p.b, precond="jacobi", tol=1e-30, maxit=5, record=5, mixed=True)
@@ -72,7 +72,7 @@ def test_mixed_with_replacement_reaches_1e10():
     """Mixed mode needs replacements (FP32 recurrences); with the relative trigger and FP64
     replacement residuals it reaches a 1e-10 true relative residual on this grid.  (It is
     not robust: on some grids, e.g. 96x96, no trigger threshold converges.)"""
-    p = tp.config2(64)
+    p = tp.problem_convdiff2d(64)
     A = p.A.to_scipy()
     m = oracle.pbicgstab(A, p.b, precond="jacobi", tol=1e-10, maxit=3000, mixed=True, rr_theta=1e-3)
     assert m.status == oracle.Status.OK and m.rel_res_true <= 1e-10

@@ -83,18 +83,18 @@ def test_random_banded_properties():
 
 
 def test_generators_deterministic():
-    a = tp.config2(16)
-    b = tp.config2(16)
+    a = tp.problem_convdiff2d(16)
+    b = tp.problem_convdiff2d(16)
     assert np.array_equal(a.b, b.b)
-    c4a = tp.config4(nsys=3, n_lo=100, n_hi=300)
-    c4b = tp.config4(nsys=3, n_lo=100, n_hi=300)
+    c4a = tp.problem_batched_banded(nsys=3, n_lo=100, n_hi=300)
+    c4b = tp.problem_batched_banded(nsys=3, n_lo=100, n_hi=300)
     for s1, s2 in zip(c4a.systems, c4b.systems):
         assert np.array_equal(s1.A.val, s2.A.val) and np.array_equal(s1.b, s2.b)
 
 
 def test_config_shapes():
-    p = tp.config1()
+    p = tp.problem_poisson2d()
     assert p.A.n == 10000 and np.allclose(p.x_star, 1 / 100.0)
     assert np.allclose(p.A.to_scipy() @ p.x_star, p.b)
-    m = tp.config5(8, 4)
+    m = tp.problem_convdiff2d_multi(8, 4)
     assert m.B.shape == (64, 4) and m.X_target.shape == (64, 4)

@@ -48,9 +48,9 @@ def _matrix(torch, capi, prob, fmt, keep):
     return m
 
 
-CASES = [("convdiff2d_128_dia_jacobi_rr", lambda: tp.config2(128), "dia", "jacobi", dict(rr_period=100)),
-         ("poisson2d_100_csr_none", lambda: tp.config1(100), "csr", "none", dict()),
-         ("convdiff2d_90_csr_jacobi_ragged", lambda: tp.config2(90), "csr", "jacobi", dict(rr_period=50))]
+CASES = [("convdiff2d_128_dia_jacobi_rr", lambda: tp.problem_convdiff2d(128), "dia", "jacobi", dict(rr_period=100)),
+         ("poisson2d_100_csr_none", lambda: tp.problem_poisson2d(100), "csr", "none", dict()),
+         ("convdiff2d_90_csr_jacobi_ragged", lambda: tp.problem_convdiff2d(90), "csr", "jacobi", dict(rr_period=50))]
 
 
 @pytest.mark.parametrize("name,maker,fmt,prec,kw", CASES)
