@@ -124,9 +124,13 @@ def measured_traffic(variant: str, workload: str):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
-    def __init__(self):
+    """nvidia-smi samples (200 ms) of SM clock, power and throttle reasons during a timed region;
+    the raw CSV goes to ``path`` (``--clocks-csv``), else to a temporary file."""
+
+    def __init__(self, path=None):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), "pbcg_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
@@ -237,7 +241,7 @@ def run_gpu(args):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        sampler = ClockSampler() if name == args.precision else None
+        sampler = ClockSampler(args.clocks_csv) if name == args.precision else None
         if sampler:
             sampler.start()
         times, ktimes, its, nrep, trues, stat = [], [], [], [], [], []
@@ -394,7 +398,7 @@ def _timed_steps(args, one, sampler_on=True):
     for _ in range(args.warmup):
         one()
     torch.cuda.synchronize()
-    sampler = ClockSampler() if sampler_on else None
+    sampler = ClockSampler(args.clocks_csv) if sampler_on else None
     if sampler:
         sampler.start()
     out = []
@@ -578,6 +582,7 @@ def main():
                          "Neumann-2; batched: 512 banded systems; autograd: differentiable solve, 16 RHS, "
                          "forward + backward")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clocks-csv", default=None, help="keep the raw nvidia-smi clock samples in this file")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
