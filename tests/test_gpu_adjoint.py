@@ -194,7 +194,7 @@ def test_autograd_matches_central_differences_small():
     assert ev.max() <= 1e-6, ev
 
 
-def test_autograd_full_size_config5():
+def test_autograd_full_size_convdiff2d_512_16rhs():
     """512x512 convection-diffusion, 16 right-hand sides, solves to 1e-12 (on this grid the
     adjoint solves' attainable accuracy is about 1e-12, so 1e-13 stalls).  Checks that hold
     at any size: forward and adjoint true residuals recomputed on the CPU, the value

@@ -34,10 +34,10 @@ def test_spmv_matches_oracle(which):
 
 # ------------------------------------------------------------------ FP64 iterates
 CASES = {
-    "config1_poisson_100x100": (lambda: tp.problem_poisson2d(), "csr", {}),
-    "config2_convdiff_128_dia": (lambda: tp.problem_convdiff2d(128), "dia", dict(rr_period=100)),
-    "config2_convdiff_97_csr_ragged": (lambda: tp.problem_convdiff2d(97), "csr", dict(rr_period=100)),
-    "config3_convdiff3d_24_neumann2": (lambda: tp.problem_convdiff3d(24), "csr", dict(rr_period=100)),
+    "poisson_100x100": (lambda: tp.problem_poisson2d(), "csr", {}),
+    "convdiff2d_128_dia": (lambda: tp.problem_convdiff2d(128), "dia", dict(rr_period=100)),
+    "convdiff2d_97_csr_ragged": (lambda: tp.problem_convdiff2d(97), "csr", dict(rr_period=100)),
+    "convdiff3d_24_neumann2": (lambda: tp.problem_convdiff3d(24), "csr", dict(rr_period=100)),
 }
 
 

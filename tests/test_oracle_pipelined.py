@@ -12,7 +12,7 @@ def _max_rel_iterate_diff(a, b, k):
     return max(np.linalg.norm(a.xs[i] - b.xs[i]) / np.linalg.norm(a.xs[i]) for i in range(k))
 
 
-def test_pipelined_equals_classic_config1_first_20():
+def test_pipelined_equals_classic_poisson_100_first_20():
     """Section 1 / Section 3: Algorithm 2 produces the iterates of Algorithm 1 in exact
     arithmetic; in FP64 they agree to <= 1e-10 relative over the first 20 iterations
     (2D Poisson 100x100, N = 10,000, x* = 1/sqrt(N), x0 = 0, no preconditioner)."""
@@ -40,7 +40,7 @@ def test_pipelined_equals_classic_preconditioned(prec, deg, maker):
     assert _max_rel_iterate_diff(c, q, 15) <= 1e-9
 
 
-def test_config1_outcomes():
+def test_poisson_100_outcomes():
     """Poisson 100x100, no preconditioner: classic reaches 1e-12; plain p-BiCGStab stops with its recursive residual
     below 1e-12 (and a true residual within 10x of it, reading R5)."""
     p = tp.problem_poisson2d()
