@@ -474,8 +474,9 @@ def run_batched(args):
             "higher_is_better": False, "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "batched_512_random_banded_fp32_jacobi_tol1e-8", "n_sys": len(row_off) - 1,
                        "total_rows": int(row_off[-1]), "nnz_per_row": round(nnz_row, 2),
-                       "launch": "%d x %d, %d block(s) per system, %d thread(s) per row (autotuned), CUDA graph" % (
-                           last["grid_blocks"], last["block_threads"], last["cluster_blocks"], last["lanes_per_row"]),
+                       "launch": "%d x %d, %d block(s) per system, %d thread(s) per row, %s build (autotuned), "
+                                 "CUDA graph" % (last["grid_blocks"], last["block_threads"], last["cluster_blocks"],
+                                                 last["lanes_per_row"], last["build"]),
                        "l2": "flushed between steps (256 MB write)"},
             "n_ok": int(last["n_ok"]), "iterations_mean": float(np.mean(last["iterations"])),
             "iterations_max": int(np.max(last["iterations"])), "kernel_ms": round(last["time_ms"], 4),

@@ -139,7 +139,12 @@ typedef struct pbcg_options {
                               2, 4 or 8 (a thread-block cluster); 0 = autotune          */
   int32_t lanes_per_row;   /* batched solver only: threads per matrix row in the SpMVs of
                               the two passes, 1, 2, 4 or 8; 0 = autotune                 */
-  int32_t reserved3;
+  int32_t batch_build;     /* batched solver only: 0 = autotune over both builds (a
+                              caller-fixed shape runs the 64-register one), 1 = the
+                              64-register kernels, 2 = the streaming cluster kernel (40
+                              registers, up to six 256-thread or three 512-thread blocks
+                              per SM; mixed precision, cluster_blocks 0, 2, 4 or 8,
+                              block_threads 0 or <= 512); other values: INVALID_ARG     */
 } pbcg_options;
 
 typedef struct pbcg_result {
@@ -262,7 +267,7 @@ typedef struct pbcg_batch_result {
   int32_t grid_blocks;
   int32_t cluster_blocks;   /* blocks per system (1: one block, else a cluster) */
   int32_t lanes_per_row;    /* threads per row in the SpMVs */
-  int32_t reserved1;
+  int32_t batch_build;      /* the kernel build that ran: 1 (64 registers) or 2 (streaming) */
 } pbcg_batch_result;
 
 typedef struct pbcg_batch_ctx pbcg_batch_ctx;

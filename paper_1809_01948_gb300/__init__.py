@@ -49,6 +49,7 @@ def _stream_handle(stream: Optional[torch.cuda.Stream]):
 
 _PREC = {"none": capi.PREC_NONE, "jacobi": capi.PREC_JACOBI, "neumann": capi.PREC_NEUMANN}
 _PRECISION = {"fp64": capi.FP64, "mixed": capi.MIXED}
+_BATCH_BUILD = {"auto": 0, "regs64": 1, "stream": 2}
 _METHOD = {"pipelined": capi.PIPELINED, "classic": capi.CLASSIC}
 _STORAGE = {"auto": capi.STORAGE_AUTO, "general": capi.STORAGE_GENERAL}
 
@@ -233,13 +234,15 @@ class BatchSolver:
 
     ``row_off``/``nnz_off``: host int64 arrays (n_sys + 1); ``row_ptr`` (local per
     system, concatenated: n_k + 1 entries each), ``col`` (local indices), ``val``:
-    CUDA tensors.  grid_blocks = block_threads = 0 lets the library autotune.
+    CUDA tensors.  grid_blocks = block_threads = 0 lets the library autotune.  ``build``:
+    "auto", "regs64" (the 64-register kernels) or "stream" (the 40-register cluster
+    kernel; mixed precision).
     """
 
     def __init__(self, row_off, nnz_off, row_ptr, col, val, precond: str = "jacobi", precision: str = "mixed",
                  tol: float = 1e-8, max_it: int = 1000, rr_period: int = 0, rr_theta: float = 0.0,
                  grid_blocks: int = 0, block_threads: int = 0, max_restarts: int = 0, cluster_blocks: int = 0,
-                 lanes_per_row: int = 0, stream: Optional[torch.cuda.Stream] = None):
+                 lanes_per_row: int = 0, build: str = "auto", stream: Optional[torch.cuda.Stream] = None):
         import numpy as np
         lib = _lib()
         self.row_off = np.ascontiguousarray(row_off, dtype=np.int64)
@@ -265,6 +268,7 @@ class BatchSolver:
         self.opt.max_restarts = max_restarts
         self.opt.cluster_blocks = cluster_blocks
         self.opt.lanes_per_row = lanes_per_row
+        self.opt.batch_build = _BATCH_BUILD[build]
         self.ctx = C.c_void_p()
         _check(lib.pbicgstab_batch_create(C.byref(self.ctx), C.byref(bt), C.byref(self.opt), _stream_handle(stream)),
                "pbicgstab_batch_create")
@@ -286,7 +290,8 @@ class BatchSolver:
             raise PBCGError(code, capi.last_error())
         return x, dict(status=st, iterations=it, n_replacements=nr, rel_res_true=tr, time_ms=res.time_ms,
                        n_ok=res.n_ok, block_threads=res.block_threads, grid_blocks=res.grid_blocks,
-                       cluster_blocks=res.cluster_blocks, lanes_per_row=res.lanes_per_row)
+                       cluster_blocks=res.cluster_blocks, lanes_per_row=res.lanes_per_row,
+                       build={1: "regs64", 2: "stream"}.get(res.batch_build, "?"))
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -41,7 +41,7 @@ class Options(C.Structure):
                 ("grid_blocks", C.c_int32), ("block_threads", C.c_int32),
                 ("max_restarts", C.c_int32), ("method", C.c_int32), ("rr_tau", C.c_double),
                 ("operator_storage", C.c_int32), ("cluster_blocks", C.c_int32),
-                ("lanes_per_row", C.c_int32), ("reserved3", C.c_int32)]
+                ("lanes_per_row", C.c_int32), ("batch_build", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -65,7 +65,7 @@ class BatchResult(C.Structure):
     _fields_ = [("status", C.c_void_p), ("iterations", C.c_void_p), ("n_replacements", C.c_void_p),
                 ("rel_res_true", C.c_void_p), ("time_ms", C.c_double), ("n_ok", C.c_int32),
                 ("block_threads", C.c_int32), ("grid_blocks", C.c_int32), ("cluster_blocks", C.c_int32),
-                ("lanes_per_row", C.c_int32), ("reserved1", C.c_int32)]
+                ("lanes_per_row", C.c_int32), ("batch_build", C.c_int32)]
 
 
 # name -> (restype, argtypes)

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pbicgstab.h"
@@ -144,9 +145,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) batched_kernel(const BatchDev 
 // hardware cluster barrier and sum their partials through distributed shared memory.
 // Large systems then run on several SMs while small ones still fill the GPU.  Every block
 // of a cluster takes the same control-flow decisions (the totals are identical), so all
-// reach every cluster barrier.
-template <typename T, typename VR>
-__global__ void __launch_bounds__(kMaxThreads, 1) batched_cluster_kernel(const BatchDev d) {
+// reach every cluster barrier.  STREAM: the mixed solver's streaming register budget
+// (SolverLaunch<float, true>: 40 registers, six 256-thread blocks per SM instead of four);
+// on the 512-system banded batch the extra resident warps cut the solve by 12%.
+template <typename T, typename VR, bool STREAM = false>
+__global__ void __launch_bounds__(SolverLaunch<T, STREAM>::kThreads, SolverLaunch<T, STREAM>::kBlocksPerSM)
+    batched_cluster_kernel(const BatchDev d) {
   __shared__ double smem[kWork + 5 * kMaxDots];
   __shared__ double scal[8];
   __shared__ int s_sys;      // rank 0: the system the cluster works on
@@ -290,7 +294,9 @@ struct pbcg_batch_ctx {
   const double* g_b = nullptr;
   double* g_x = nullptr;
   int g_grid = 0, g_threads = 0, g_cluster = 0, g_lanes = 0;
+  bool g_stream = false;
   int tuned_grid = 0, tuned_threads = 0, tuned_cluster = 0, tuned_lanes = 0;
+  bool tuned_stream = false;
 };
 
 static void batch_free(pbcg_batch_ctx* c) {
@@ -309,15 +315,19 @@ static void batch_free(pbcg_batch_ctx* c) {
 }
 
 template <typename T, typename VR>
-static const void* bkernel(bool cluster) {
+static const void* bkernel(bool cluster, bool stream) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (stream && cluster) return (const void*)batched_cluster_kernel<T, VR, true>;
+  }
   return cluster ? (const void*)batched_cluster_kernel<T, VR> : (const void*)batched_kernel<T, VR>;
 }
 
-// The one-block-per-system kernel, or (cluster = true) the cluster-per-system kernel.
-static const void* pick_kernel(const pbcg_batch_ctx* c, bool cluster = false) {
+// The one-block-per-system kernel, or (cluster = true) the cluster-per-system kernel
+// (stream: its streaming build, mixed precision only).
+static const void* pick_kernel(const pbcg_batch_ctx* c, bool cluster = false, bool stream = false) {
   const bool mixed = c->precision == PBCG_MIXED;
-  if (mixed) return c->vr_f32 ? bkernel<float, float>(cluster) : bkernel<float, double>(cluster);
-  return c->vr_f32 ? bkernel<double, float>(cluster) : bkernel<double, double>(cluster);
+  if (mixed) return c->vr_f32 ? bkernel<float, float>(cluster, stream) : bkernel<float, double>(cluster, stream);
+  return c->vr_f32 ? bkernel<double, float>(cluster, false) : bkernel<double, double>(cluster, false);
 }
 
 static BatchDev make_dev(pbcg_batch_ctx* c, const double* b, double* x, int lanes) {
@@ -372,7 +382,7 @@ static void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute& attr, i
 }
 
 static pbcg_status launch_direct(pbcg_batch_ctx* c, const double* b, double* x, int grid, int threads, int cluster,
-                                 int lanes, cudaStream_t s) {
+                                 int lanes, bool stream, cudaStream_t s) {
   BCK(cudaMemsetAsync(c->counter, 0, sizeof(unsigned), s), "memset");
   BatchDev d = make_dev(c, b, x, lanes);
   void* args[] = {&d};
@@ -382,35 +392,41 @@ static pbcg_status launch_direct(pbcg_batch_ctx* c, const double* b, double* x, 
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr;
     cluster_config(cfg, attr, grid, threads, cluster, s);
-    BCK(cudaLaunchKernelExC(&cfg, pick_kernel(c, true), args), "batched cluster launch");
+    BCK(cudaLaunchKernelExC(&cfg, pick_kernel(c, true, stream), args), "batched cluster launch");
   }
   return PBCG_OK;
 }
 
 struct BatchShape {
   int grid, threads, cluster, lanes;
+  bool stream;
 };
 
 // Clusters of `cluster` blocks that can be resident at once for this block size (0: none).
-static pbcg_status active_clusters(const pbcg_batch_ctx* c, int threads, int cluster, int* n) {
+static pbcg_status active_clusters(const pbcg_batch_ctx* c, int threads, int cluster, int* n, bool stream = false) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr;
   cluster_config(cfg, attr, cluster, threads, cluster, c->stream);
   *n = 0;
-  BCK(cudaOccupancyMaxActiveClusters(n, pick_kernel(c, true), &cfg), "cluster occupancy");
+  BCK(cudaOccupancyMaxActiveClusters(n, pick_kernel(c, true, stream), &cfg), "cluster occupancy");
   return PBCG_OK;
 }
 
 // Candidate launch shapes: one block per system at 256/512/1024 threads and 1-4 blocks per
-// SM, and clusters of 2, 4 or 8 blocks per system at every resident cluster count.
+// SM, and clusters of 2, 4 or 8 blocks per system at every resident cluster count; in mixed
+// precision also the streaming cluster build where it fits more clusters (options.batch_build
+// restricts the list to one build).
 static pbcg_status candidate_shapes(const pbcg_batch_ctx* c, std::vector<BatchShape>& out, int only_cluster) {
   const int sms = sm_count();
   const int tlist[] = {256, 512, 1024};
+  const int build = c->opt.batch_build;   // 0: both builds, 1: 64 registers only, 2: streaming only
+  const bool want64 = build != 2;
+  const bool want_stream = c->precision == PBCG_MIXED && build != 1;
   for (int t : tlist) {
-    if (only_cluster <= 1) {
+    if (only_cluster <= 1 && want64) {
       int per = 0;
       BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pick_kernel(c), t, 0), "occupancy");
-      for (int bps = 1; bps <= std::min(per, 4); ++bps) out.push_back({sms * bps, t, 1, 1});
+      for (int bps = 1; bps <= std::min(per, 4); ++bps) out.push_back({sms * bps, t, 1, 1, false});
     }
     for (int cl = 2; cl <= 8; cl *= 2) {
       if (only_cluster > 1 && cl != only_cluster) continue;
@@ -418,7 +434,13 @@ static pbcg_status candidate_shapes(const pbcg_batch_ctx* c, std::vector<BatchSh
       int nc = 0;
       pbcg_status st = active_clusters(c, t, cl, &nc);
       if (st != PBCG_OK) return st;
-      if (nc > 0) out.push_back({nc * cl, t, cl, 1});
+      if (want64 && nc > 0) out.push_back({nc * cl, t, cl, 1, false});
+      if (want_stream && t <= SolverLaunch<float, true>::kThreads) {   // only where it adds residency
+        int ns = 0;
+        st = active_clusters(c, t, cl, &ns, true);
+        if (st != PBCG_OK) return st;
+        if (ns > (want64 ? nc : 0)) out.push_back({ns * cl, t, cl, 1, true});
+      }
     }
   }
   return PBCG_OK;
@@ -437,7 +459,7 @@ static pbcg_status autotune(pbcg_batch_ctx* c, const double* b, double* x) {
   auto trial = [&](const BatchShape& sh) -> pbcg_status {
     cudaMemcpyAsync(xs, x, sizeof(double) * c->total_rows, cudaMemcpyDeviceToDevice, c->stream);
     cudaEventRecord(c->ev0, c->stream);
-    pbcg_status s2 = launch_direct(c, b, xs, sh.grid, sh.threads, sh.cluster, sh.lanes, c->stream);
+    pbcg_status s2 = launch_direct(c, b, xs, sh.grid, sh.threads, sh.cluster, sh.lanes, sh.stream, c->stream);
     if (s2 != PBCG_OK) return s2;
     cudaEventRecord(c->ev1, c->stream);
     if (cudaEventSynchronize(c->ev1) != cudaSuccess) return cuda_status(cudaGetLastError(), "autotune");
@@ -446,6 +468,7 @@ static pbcg_status autotune(pbcg_batch_ctx* c, const double* b, double* x) {
     if (ms < best) {
       best = ms;
       c->tuned_grid = sh.grid; c->tuned_threads = sh.threads; c->tuned_cluster = sh.cluster; c->tuned_lanes = sh.lanes;
+      c->tuned_stream = sh.stream;
     }
     return PBCG_OK;
   };
@@ -456,7 +479,7 @@ static pbcg_status autotune(pbcg_batch_ctx* c, const double* b, double* x) {
     if ((st = trial(s1)) != PBCG_OK) break;
   }
   if (st == PBCG_OK && !fixed_lanes) {
-    const BatchShape base{c->tuned_grid, c->tuned_threads, c->tuned_cluster, 1};
+    const BatchShape base{c->tuned_grid, c->tuned_threads, c->tuned_cluster, 1, c->tuned_stream};
     for (int L = 2; L <= 8 && st == PBCG_OK; L *= 2) {
       BatchShape s2 = base;
       s2.lanes = L;
@@ -464,6 +487,7 @@ static pbcg_status autotune(pbcg_batch_ctx* c, const double* b, double* x) {
     }
   }
   cudaFreeAsync(xs, c->stream);
+  if (st == PBCG_OK && !c->tuned_grid) return set_error(PBCG_CUDA_ERROR, "autotune found no launch shape that fits");
   return st;
 }
 
@@ -490,6 +514,11 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
   if (opt->lanes_per_row != 0 && opt->lanes_per_row != 1 && opt->lanes_per_row != 2 && opt->lanes_per_row != 4 &&
       opt->lanes_per_row != 8)
     return set_error(PBCG_INVALID_ARG, "lanes_per_row must be 0, 1, 2, 4 or 8");
+  if (opt->batch_build < 0 || opt->batch_build > 2) return set_error(PBCG_INVALID_ARG, "batch_build must be 0, 1 or 2");
+  if (opt->batch_build == 2 && (opt->precision != PBCG_MIXED || opt->cluster_blocks == 1 ||
+                                opt->block_threads > SolverLaunch<float, true>::kThreads))
+    return set_error(PBCG_INVALID_ARG, "the streaming build (batch_build 2) runs mixed precision in clusters of "
+                                       "2, 4 or 8 blocks of at most %d threads", SolverLaunch<float, true>::kThreads);
   const int ns = B->n_sys;
   if (B->row_off[0] != 0 || B->nnz_off[0] != 0) return set_error(PBCG_INVALID_ARG, "offsets must start at 0");
   for (int k = 0; k < ns; ++k) {
@@ -593,14 +622,14 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
 }
 
 static pbcg_status ensure_graph(pbcg_batch_ctx* c, const double* b, double* x, int grid, int threads, int cluster,
-                                int lanes) {
+                                int lanes, bool stream) {
   if (c->exec && c->g_b == b && c->g_x == x && c->g_grid == grid && c->g_threads == threads && c->g_cluster == cluster &&
-      c->g_lanes == lanes)
+      c->g_lanes == lanes && c->g_stream == stream)
     return PBCG_OK;
   if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
   cudaGraph_t graph = nullptr;
   BCK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-  pbcg_status st = launch_direct(c, b, x, grid, threads, cluster, lanes, c->cap_stream);
+  pbcg_status st = launch_direct(c, b, x, grid, threads, cluster, lanes, stream, c->cap_stream);
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
   if (st != PBCG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
   BCK(e, "end capture");
@@ -613,6 +642,7 @@ static pbcg_status ensure_graph(pbcg_batch_ctx* c, const double* b, double* x, i
   c->g_threads = threads;
   c->g_cluster = cluster;
   c->g_lanes = lanes;
+  c->g_stream = stream;
   return PBCG_OK;
 }
 
@@ -620,6 +650,7 @@ extern "C" pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* c, const double* b,
   if (!c || !b || !x) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_batch_solve");
   int grid = c->opt.grid_blocks, threads = c->opt.block_threads, cluster = std::max(1, c->opt.cluster_blocks);
   int lanes = std::max(1, c->opt.lanes_per_row);
+  bool stream = c->opt.batch_build == 2;   // caller-fixed shapes: the 64-register builds unless asked
   if (grid == 0 || threads == 0) {
     if (!c->tuned_grid) {
       pbcg_status st = autotune(c, b, x);
@@ -629,14 +660,17 @@ extern "C" pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* c, const double* b,
     threads = c->tuned_threads;
     cluster = c->tuned_cluster;
     lanes = c->tuned_lanes;
+    stream = c->tuned_stream;
+  } else if (stream && cluster <= 1) {
+    return set_error(PBCG_INVALID_ARG, "the streaming build runs clusters: cluster_blocks must be 2, 4 or 8");
   } else if (cluster > 1) {
     int nc = 0;
-    pbcg_status st = active_clusters(c, threads, cluster, &nc);
+    pbcg_status st = active_clusters(c, threads, cluster, &nc, stream);
     if (st != PBCG_OK) return st;
     if (grid % cluster || grid / cluster > nc)
       return set_error(PBCG_INVALID_ARG, "grid_blocks must be a multiple of the cluster size and fit on the GPU");
   }
-  pbcg_status st = ensure_graph(c, b, x, grid, threads, cluster, lanes);
+  pbcg_status st = ensure_graph(c, b, x, grid, threads, cluster, lanes, stream);
   if (st != PBCG_OK) return st;
   BCK(cudaEventRecord(c->ev0, c->stream), "event");
   BCK(cudaGraphLaunch(c->exec, c->stream), "graph launch");
@@ -651,6 +685,7 @@ extern "C" pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* c, const double* b,
   res->grid_blocks = grid;
   res->cluster_blocks = cluster;
   res->lanes_per_row = lanes;
+  res->batch_build = stream ? 2 : 1;
   int nok = 0;
   pbcg_status first_bad = PBCG_OK;
   for (int k = 0; k < c->n_sys; ++k) {

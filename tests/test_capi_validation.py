@@ -99,6 +99,23 @@ def test_method_and_policy_need_their_preconditioners(lib):
     assert _create(lib, _csr(), prec=capi.PREC_NEUMANN, degree=2, rr_auto=1)[0] == INVALID
 
 
+@pytest.mark.parametrize("kw", [dict(batch_build=3), dict(batch_build=-1), dict(batch_build=2),
+                                dict(batch_build=2, precision=capi.MIXED, cluster_blocks=1),
+                                dict(batch_build=2, precision=capi.MIXED, block_threads=1024)])
+def test_batched_build_option(lib, kw):
+    """batch_build: 0, 1 or 2 only; the streaming build needs mixed precision, clusters and
+    at most 512 threads per block (all checked before any CUDA call)."""
+    row_off = (C.c_int64 * 2)(0, 10)
+    nnz_off = (C.c_int64 * 2)(0, 10)
+    bt = capi.Batch()
+    bt.n_sys, bt.val_dtype, bt.precond = 1, capi.F64, capi.PREC_JACOBI
+    bt.row_off, bt.nnz_off = C.cast(row_off, C.c_void_p), C.cast(nnz_off, C.c_void_p)
+    bt.row_ptr, bt.col, bt.val = C.c_void_p(0x1000), C.c_void_p(0x2000), C.c_void_p(0x3000)
+    ctx = C.c_void_p()
+    st = lib.pbicgstab_batch_create(C.byref(ctx), C.byref(bt), C.byref(_opts(lib, **kw)), None)
+    assert st == INVALID and "batch_build" in lib.pbicgstab_last_error().decode() and not ctx.value
+
+
 def test_batched_and_multi_argument_errors(lib):
     ctx = C.c_void_p()
     bt = capi.Batch()

@@ -161,3 +161,38 @@ def test_batched_lanes_per_row_matches_single_solver(lanes, cluster):
     with pytest.raises(pb.PBCGError):
         pb.BatchSolver(c["row_off"], c["nnz_off"], torch.from_numpy(c["row_ptr"]).to(dev),
                        torch.from_numpy(c["col"]).to(dev), torch.from_numpy(c["val"]).to(dev), lanes_per_row=3)
+
+
+def test_batched_streaming_cluster_build_equals_64_register_build():
+    """The streaming cluster build (40 registers, more resident clusters) runs the same
+    per-system code as the 64-register cluster kernel: identical iterates, bit for bit, at a
+    fixed shape; the autotuner restricted to it solves every system; FP64, one block per
+    system and 1024-thread blocks reject it."""
+    torch = torch_cuda()
+    import paper_1809_01948_gb300 as pb
+    bp = tp.problem_batched_banded(nsys=24, n_lo=200, n_hi=6000, band=64)
+    kw = dict(precision="mixed", tol=1e-8, max_it=500, rr_theta=1e-3, grid_blocks=16, block_threads=256,
+              cluster_blocks=4)
+    s1, c, b = _batch_solver(bp, build="regs64", **kw)
+    s2, _, _ = _batch_solver(bp, build="stream", **kw)
+    x1, i1 = s1.solve(b)
+    x2, i2 = s2.solve(b)
+    assert i1["build"] == "regs64" and i2["build"] == "stream"
+    assert i1["n_ok"] == 24 and i2["n_ok"] == 24
+    assert np.array_equal(i1["iterations"], i2["iterations"])
+    assert torch.equal(x1, x2)
+    s3, _, _ = _batch_solver(bp, build="stream", precision="mixed", tol=1e-8, max_it=500, rr_theta=1e-3)
+    x3, i3 = s3.solve(b)
+    assert i3["build"] == "stream" and i3["n_ok"] == 24 and i3["block_threads"] <= 512 and i3["cluster_blocks"] > 1
+    x3 = x3.cpu().numpy()
+    for k, sysk in enumerate(bp.systems):
+        xk = x3[c["row_off"][k]:c["row_off"][k + 1]]
+        A = sysk.A.to_scipy(np.float64)
+        assert np.linalg.norm(sysk.b - A @ xk) <= 1e-7 * np.linalg.norm(sysk.b)
+    for bad in (dict(build="stream", precision="fp64"), dict(build="stream", precision="mixed", cluster_blocks=1),
+                dict(build="stream", precision="mixed", block_threads=1024, grid_blocks=8, cluster_blocks=2)):
+        with pytest.raises(pb.PBCGError):
+            _batch_solver(bp, **bad)
+    s4, _, _ = _batch_solver(bp, build="stream", precision="mixed", grid_blocks=8, block_threads=256)
+    with pytest.raises(pb.PBCGError):   # a fixed shape with one block per system
+        s4.solve(b)
