@@ -682,21 +682,19 @@ extern "C" pbcg_status pbicgstab_solve(pbcg_ctx* c, const double* b, double* x, 
 
 extern "C" pbcg_status pbicgstab_solve_host(pbcg_ctx* c, const double* b_host, double* x_host, pbcg_result* res) {
   if (!c || !b_host || !x_host || !res) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_solve_host");
-  // b and x live in the spare tail of the workspace-sized staging buffers below
+  // stream-ordered device copies of b and x for this call, freed on every path
   double* db = nullptr;
   double* dx = nullptr;
   const size_t bytes = sizeof(double) * (size_t)c->n;
-  CK(cudaMallocAsync((void**)&db, bytes, c->stream), "cudaMallocAsync b");
-  CK(cudaMallocAsync((void**)&dx, bytes, c->stream), "cudaMallocAsync x");
-  CK(cudaMemcpyAsync(db, b_host, bytes, cudaMemcpyHostToDevice, c->stream), "copy b");
-  CK(cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, c->stream), "copy x0");
-  pbcg_status st = enqueue_solve(c, db, dx);
-  if (st == PBCG_OK) {
-    CK(cudaMemcpyAsync(x_host, dx, bytes, cudaMemcpyDeviceToHost, c->stream), "copy x");
-    st = collect(c, res);
-  }
-  cudaFreeAsync(db, c->stream);
-  cudaFreeAsync(dx, c->stream);
+  pbcg_status st = cuda_status(cudaMallocAsync((void**)&db, bytes, c->stream), "cudaMallocAsync b");
+  if (st == PBCG_OK) st = cuda_status(cudaMallocAsync((void**)&dx, bytes, c->stream), "cudaMallocAsync x");
+  if (st == PBCG_OK) st = cuda_status(cudaMemcpyAsync(db, b_host, bytes, cudaMemcpyHostToDevice, c->stream), "copy b");
+  if (st == PBCG_OK) st = cuda_status(cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, c->stream), "copy x0");
+  if (st == PBCG_OK) st = enqueue_solve(c, db, dx);
+  if (st == PBCG_OK) st = cuda_status(cudaMemcpyAsync(x_host, dx, bytes, cudaMemcpyDeviceToHost, c->stream), "copy x");
+  if (st == PBCG_OK) st = collect(c, res);
+  if (db) cudaFreeAsync(db, c->stream);
+  if (dx) cudaFreeAsync(dx, c->stream);
   cudaStreamSynchronize(c->stream);
   return st;
 }
@@ -723,20 +721,20 @@ extern "C" pbcg_status pbicgstab_test_barrier_timeout(double timeout_ms, int32_t
     return set_error(PBCG_INVALID_ARG, "need extra >= 1, 0 < timeout_ms <= 10000 and a status pointer");
   unsigned* bar = nullptr;
   int* err = nullptr;
-  CK(cudaMalloc(&bar, sizeof(unsigned)), "cudaMalloc");
-  CK(cudaMalloc(&err, sizeof(int)), "cudaMalloc");
-  CK(cudaMemset(bar, 0, sizeof(unsigned)), "memset");
-  CK(cudaMemset(err, 0, sizeof(int)), "memset");
+  cudaError_t e = cudaMalloc(&bar, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(bar, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
   const int grid = sm_count();
   unsigned long long tns = (unsigned long long)(timeout_ms * 1e6);
   int ex = extra;
   void* args[] = {&bar, &err, &ex, &tns};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)barrier_timeout_kernel, grid, 64, args, 0, 0);
+  if (e == cudaSuccess) e = cudaLaunchCooperativeKernel((const void*)barrier_timeout_kernel, grid, 64, args, 0, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   int h = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
-  cudaFree(bar);
-  cudaFree(err);
+  if (bar) cudaFree(bar);
+  if (err) cudaFree(err);
   CK(e, "barrier timeout kernel");
   *kernel_status = h ? PBCG_TIMEOUT : PBCG_OK;
   return PBCG_OK;
