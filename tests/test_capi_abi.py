@@ -40,7 +40,8 @@ def test_binding_covers_header():
 def test_struct_layouts_match_c():
     from paper_1809_01948_gb300 import _capi
     structs = {"pbcg_matrix": _capi.Matrix, "pbcg_precond": _capi.Precond,
-               "pbcg_options": _capi.Options, "pbcg_result": _capi.Result}
+               "pbcg_options": _capi.Options, "pbcg_result": _capi.Result,
+               "pbcg_batch": _capi.Batch, "pbcg_batch_result": _capi.BatchResult}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pbicgstab.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
