@@ -18,6 +18,12 @@ the convention under which the paper's bounds include the SpMV and PREC
 round-off terms and under which the gap recurrences hold exactly.  "Exact" is
 evaluated in numpy's extended ``longdouble`` (64-bit mantissa on x86); the
 probes refuse to run where longdouble is no wider than double.
+
+Parity status: the local-error definitions, the gaps and the gap recurrences are
+pinned by equalities (the recurrences hold to the extended precision on real runs).
+``delta_bounds`` and ``bound_constants`` are upper bounds and are pinned by
+inequalities only (measured errors below them): "parity partially pinned" -- a term
+that does not dominate its bound could be dropped without a pin failing.
 """
 from __future__ import annotations
 
