@@ -423,6 +423,9 @@ class _GapBound:
     replacement, are the round-off bounds of the explicitly computed vectors:
     F^z = mu sqrt(N) ||A|| ||l|| eps, F^w = mu sqrt(N) ||A|| ||k|| eps,
     F^s = mu sqrt(N) ||A|| ||g|| eps and f^r = ((mu sqrt(N) + 1) ||A|| ||x|| + ||b||) eps.
+
+    Parity partially pinned: f^r is an upper bound and its pins are inequalities
+    (||Delta^r_i|| <= f^r_i on every iteration of real runs, and after a replacement).
     """
 
     def __init__(self, A64, M, b, eps, mixed):
