@@ -457,14 +457,15 @@ static pbcg_status autotune(pbcg_batch_ctx* c, const double* b, double* x) {
   BCK(cudaMallocAsync((void**)&xs, sizeof(double) * c->total_rows, c->stream), "autotune scratch");
   float best = 1e30f;
   auto trial = [&](const BatchShape& sh) -> pbcg_status {
-    cudaMemcpyAsync(xs, x, sizeof(double) * c->total_rows, cudaMemcpyDeviceToDevice, c->stream);
-    cudaEventRecord(c->ev0, c->stream);
-    pbcg_status s2 = launch_direct(c, b, xs, sh.grid, sh.threads, sh.cluster, sh.lanes, sh.stream, c->stream);
-    if (s2 != PBCG_OK) return s2;
-    cudaEventRecord(c->ev1, c->stream);
-    if (cudaEventSynchronize(c->ev1) != cudaSuccess) return cuda_status(cudaGetLastError(), "autotune");
+    pbcg_status s2 = cuda_status(cudaMemcpyAsync(xs, x, sizeof(double) * c->total_rows, cudaMemcpyDeviceToDevice,
+                                                 c->stream), "autotune copy");
+    if (s2 == PBCG_OK) s2 = cuda_status(cudaEventRecord(c->ev0, c->stream), "event");
+    if (s2 == PBCG_OK) s2 = launch_direct(c, b, xs, sh.grid, sh.threads, sh.cluster, sh.lanes, sh.stream, c->stream);
+    if (s2 == PBCG_OK) s2 = cuda_status(cudaEventRecord(c->ev1, c->stream), "event");
+    if (s2 == PBCG_OK) s2 = cuda_status(cudaEventSynchronize(c->ev1), "autotune");
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    if (s2 == PBCG_OK) s2 = cuda_status(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "event timing");
+    if (s2 != PBCG_OK) return s2;
     if (ms < best) {
       best = ms;
       c->tuned_grid = sh.grid; c->tuned_threads = sh.threads; c->tuned_cluster = sh.cluster; c->tuned_lanes = sh.lanes;
