@@ -175,7 +175,10 @@ pbcg_status pbicgstab_create(pbcg_ctx** out, const pbcg_matrix* A, const pbcg_pr
 
 /* Replace the solve options (tolerance, iteration limit, replacement policy,
  * history buffers, launch shape) of an existing context.  The precision and the
- * operator storage cannot change.  ctx, opt: host, non-NULL. */
+ * operator storage cannot change.  ctx, opt: host, non-NULL; opt is copied.
+ * Errors: INVALID_ARG (NULL, an option out of range, a precision or storage
+ * change, a method or policy the preconditioner does not allow); the context
+ * keeps its previous options then. */
 pbcg_status pbicgstab_set_options(pbcg_ctx* ctx, const pbcg_options* opt);
 
 /* Solve A x = b with p-BiCGStab (Algorithm 2 with Eq. rr replacements per the
@@ -183,13 +186,20 @@ pbcg_status pbicgstab_set_options(pbcg_ctx* ctx, const pbcg_options* opt);
  * PBCG_CLASSIC.  b: device, n doubles, read only.  x: device, n doubles, read as
  * x0 and overwritten with the last iterate (the solution on PBCG_OK).  res: host
  * or NULL; when non-NULL the call waits for the solve and fills it, otherwise it
- * only enqueues the work.  The returned status is the solve's status when res is
- * given, else PBCG_OK once the launch succeeded. */
+ * only enqueues the work.  The caller keeps ownership of b and x and must keep
+ * them alive until the stream has passed the solve.  The returned status is the
+ * solve's status when res is given (OK, NOT_CONVERGED, BREAKDOWN, STAGNATED,
+ * TIMEOUT), else PBCG_OK once the launch succeeded; INVALID_ARG for NULL
+ * arguments or a launch shape the device cannot co-schedule, CUDA_ERROR when a
+ * launch or copy fails. */
 pbcg_status pbicgstab_solve(pbcg_ctx* ctx, const double* b, double* x, pbcg_result* res);
 
 /* Same as pbicgstab_solve with b and x in HOST memory (pinned or pageable): the
  * host-to-device copy of b and x0, the solve and the device-to-host copy of x are
- * enqueued on the context's stream and waited for.  res: host, non-NULL. */
+ * enqueued on the context's stream and waited for.  res: host, non-NULL.  The
+ * device copies are stream-ordered allocations of this call, freed before it
+ * returns on every path.  Errors: as pbicgstab_solve, plus OUT_OF_MEMORY /
+ * CUDA_ERROR from the staging allocations and copies. */
 pbcg_status pbicgstab_solve_host(pbcg_ctx* ctx, const double* b_host, double* x_host,
                                  pbcg_result* res);
 
@@ -200,30 +210,42 @@ pbcg_status pbicgstab_solve_host(pbcg_ctx* ctx, const double* b_host, double* x_
  * team per right-hand side, each with its own barrier and reductions; more than
  * (co-resident blocks) right-hand sides run in waves.  res: host array of nrhs
  * results or NULL; time_ms of every entry is the total kernel time.  Waits.
- * Returns PBCG_OK when every column converged, else the first failing status. */
+ * The context keeps the multi-RHS workspace (15 n-vectors per team) until it is
+ * destroyed.  Returns PBCG_OK when every column converged, else the first failing
+ * status; INVALID_ARG for NULL arguments, nrhs < 1, options.rr_auto or
+ * PBCG_CLASSIC; TIMEOUT when a team barrier gave up. */
 pbcg_status pbicgstab_solve_multi(pbcg_ctx* ctx, int32_t nrhs, const double* B, double* X,
                                   pbcg_result* res);
 
 /* Create a context for the transposed matrix A^T (CSR only) with the same
  * preconditioner kind and options: the adjoint solve A^T lambda = dL/dx of a
  * differentiable solve.  A^T is built on the device (column counts, scan,
- * scatter, and a per-row sort that makes it independent of atomic order). */
+ * scatter, and a per-row sort that makes it independent of atomic order).  *out
+ * is a new, independent context (release it with pbicgstab_destroy); src is not
+ * modified.  Errors: INVALID_ARG (NULL, or src not CSR), OUT_OF_MEMORY,
+ * CUDA_ERROR, or any error of pbicgstab_create for A^T (e.g. a zero diagonal). */
 pbcg_status pbicgstab_create_transpose(pbcg_ctx** out, const pbcg_ctx* src);
 
 /* Gradient of a loss with respect to the stored CSR values of the context's
  * matrix, given the adjoint solutions Lam (A^T Lam = dL/dX) and the solutions X
  * (device, column-major n x nrhs):  grad[e] = - sum_c Lam[row_e, c] X[col_e, c]
- * for every stored entry e in CSR order (device, nnz doubles).  Stream-ordered. */
+ * for every stored entry e in CSR order (device, nnz doubles).  Stream-ordered.
+ * Errors: INVALID_ARG (NULL, nrhs < 1, or a DIA context), CUDA_ERROR. */
 pbcg_status pbicgstab_csr_value_grad(pbcg_ctx* ctx, int32_t nrhs, const double* Lam, const double* X,
                                      double* grad);
 
-/* y = A x with the context's FP64 matrix (x, y: device, n doubles). */
+/* y = A x with the context's FP64 matrix (the SPMV of Algorithm 2; x, y: device,
+ * n doubles, must not overlap).  Stream-ordered.  Errors: INVALID_ARG (NULL),
+ * CUDA_ERROR. */
 pbcg_status pbicgstab_spmv(pbcg_ctx* ctx, const double* x, double* y);
 
-/* *rel = ||b - A x|| / ||b|| in FP64 (b, x: device; rel: host).  Waits. */
+/* *rel = ||b - A x|| / ||b|| in FP64, the true relative residual whose gap to the
+ * recursive residual Section 3 analyses (b, x: device; rel: host).  Waits.
+ * Errors: INVALID_ARG (NULL), CUDA_ERROR. */
 pbcg_status pbicgstab_true_residual(pbcg_ctx* ctx, const double* b, const double* x, double* rel);
 
-/* Release everything the context owns.  NULL is accepted. */
+/* Release everything the context owns after waiting for its stream.  NULL is
+ * accepted.  Always returns PBCG_OK. */
 pbcg_status pbicgstab_destroy(pbcg_ctx* ctx);
 
 /* Thread-local description of the last failure in this thread ("" if none). */
@@ -232,8 +254,9 @@ const char* pbicgstab_last_error(void);
 /* ---------------------------------------------------------------------------
  * Batched solves: many independent systems A_k x_k = b_k of different sizes,
  * solved by one persistent kernel launch (replayed from a CUDA graph).  Each
- * system is solved by one thread block running Algorithm 2 with Eq. (rr)
- * replacements; blocks take systems from a device queue, largest first.
+ * system is solved by one thread block, or one thread-block cluster of 2, 4 or 8
+ * blocks, running Algorithm 2 with Eq. (rr) replacements; blocks (clusters) take
+ * systems from a device queue, largest first.
  *
  * Storage: the systems' CSR matrices are concatenated.  For system k (0-based):
  *   rows       row_off[k] .. row_off[k+1]-1 of the concatenated b and x,
@@ -273,24 +296,33 @@ typedef struct pbcg_batch_result {
 typedef struct pbcg_batch_ctx pbcg_batch_ctx;
 
 /* Validate and prepare a batch (copies of the matrices, D^{-1}, A D^{-1}, FP32
- * copies in mixed mode, workspace, queue order).  opt: precision, tol, max_it,
- * replacement policy; grid_blocks / block_threads = 0 request the autotuner
- * (it times the candidate launch shapes on the first solve and keeps the
- * fastest).  History options are ignored.  Errors: INVALID_ARG, OUT_OF_MEMORY,
- * CUDA_ERROR. */
+ * copies in mixed mode, workspace, queue order).  The library copies everything it
+ * needs: the caller may free its arrays once the call returns.  opt: precision,
+ * tol, max_it, replacement policy (periodic / relative; not rr_auto), method
+ * PBCG_PIPELINED only, cluster_blocks, lanes_per_row, batch_build; grid_blocks /
+ * block_threads = 0 request the autotuner (it times the candidate launch shapes on
+ * the first solve and keeps the fastest).  History options are ignored.  Errors:
+ * INVALID_ARG (NULL, n_sys < 1, a system of size 0 or >= 2^31-1, decreasing
+ * offsets, an invalid matrix found by the device validation, an option out of
+ * range), OUT_OF_MEMORY, CUDA_ERROR; *out is NULL then. */
 pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_batch* batch,
                                    const pbcg_options* opt, void* stream);
 
 /* Solve all systems: b (device, sum n_k doubles), x (device, read as x0 and
  * overwritten).  res: host or NULL (NULL: enqueue only).  The launch is a CUDA
  * graph replay after the first call with the same b and x pointers.  Returns
- * PBCG_OK when every system converged, else the first failing status found. */
+ * PBCG_OK when every system converged, else the first failing status found
+ * (per-system statuses in res->status); INVALID_ARG for NULL arguments or a
+ * caller-fixed shape that does not fit, CUDA_ERROR when a launch fails. */
 pbcg_status pbicgstab_batch_solve(pbcg_batch_ctx* ctx, const double* b, double* x,
                                   pbcg_batch_result* res);
 
+/* Release everything the batch context owns (after waiting for its stream),
+ * including its CUDA graph.  NULL is accepted.  Always returns PBCG_OK. */
 pbcg_status pbicgstab_batch_destroy(pbcg_batch_ctx* ctx);
 
-/* One-shot convenience: create, solve, destroy. */
+/* One-shot convenience: create, solve (waits when res is NULL too), destroy.
+ * Errors: those of pbicgstab_batch_create and pbicgstab_batch_solve. */
 pbcg_status pbicgstab_solve_batched(const pbcg_batch* batch, const pbcg_options* opt, void* stream,
                                     const double* b, double* x, pbcg_batch_result* res);
 
@@ -306,7 +338,7 @@ pbcg_status pbicgstab_solve_batched(const pbcg_batch* batch, const pbcg_options*
  * D^{-1}, the operator A D^{-1}, reduction partials, barrier and result state)
  * lives in one fixed array of device memory that the library declares
  * statically.  That array is reserved on every GPU that loads the library, for
- * as long as the process runs: about 8.6 MB.  The call allocates nothing (no
+ * as long as the process runs: 9,044,224 bytes (8.6 MiB).  The call allocates nothing (no
  * cudaMalloc, cudaFree or allocating library routine) and keeps no reference to
  * the caller's arrays after it returns.
  *
