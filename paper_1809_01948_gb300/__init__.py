@@ -42,6 +42,15 @@ def _ptr(t: Optional[torch.Tensor]):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _need_cuda(t, name: str, dtype=torch.float64, numel: Optional[int] = None):
+    """The library reads these arrays on the device: reject host tensors, other dtypes,
+    strided views and wrong sizes before any call into it."""
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and (dtype is None or t.dtype == dtype)
+            and t.is_contiguous() and (numel is None or t.numel() == numel)):
+        raise ValueError("%s must be a contiguous CUDA %s tensor%s" % (
+            name, dtype if dtype is not None else "", "" if numel is None else " of %d elements" % numel))
+
+
 def _stream_handle(stream: Optional[torch.cuda.Stream]):
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
@@ -200,6 +209,11 @@ class Solver:
 
     def value_grad(self, Lam: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
         """-sum_c Lam[row_e, c] X[col_e, c] over the stored CSR entries (``pbicgstab_csr_value_grad``)."""
+        if not (isinstance(X, torch.Tensor) and isinstance(Lam, torch.Tensor) and X.dim() == 2
+                and Lam.shape == X.shape and X.shape[0] == self.n):
+            raise ValueError("Lam and X must both have shape (n, nrhs)")
+        _need_cuda(Lam.contiguous(), "Lam")
+        _need_cuda(X.contiguous(), "X")
         nrhs = X.shape[1]
         Lc = Lam.t().contiguous()
         Xc = X.t().contiguous()
@@ -208,11 +222,17 @@ class Solver:
         return g
 
     def spmv(self, x: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
+        _need_cuda(x, "x", numel=self.n)
         y = torch.empty_like(x) if y is None else y
+        _need_cuda(y, "y", numel=self.n)
+        if y.data_ptr() == x.data_ptr():
+            raise ValueError("y must not alias x")
         _check(_lib().pbicgstab_spmv(self.ctx, _ptr(x), _ptr(y)), "pbicgstab_spmv")
         return y
 
     def true_residual(self, b: torch.Tensor, x: torch.Tensor) -> float:
+        _need_cuda(b, "b", numel=self.n)
+        _need_cuda(x, "x", numel=self.n)
         out = C.c_double()
         _check(_lib().pbicgstab_true_residual(self.ctx, _ptr(b), _ptr(x), C.byref(out)), "true_residual")
         return out.value
@@ -249,6 +269,14 @@ class BatchSolver:
         self.nnz_off = np.ascontiguousarray(nnz_off, dtype=np.int64)
         self.n_sys = len(self.row_off) - 1
         self.total_rows = int(self.row_off[-1])
+        for t, name in ((row_ptr, "row_ptr"), (col, "col"), (val, "val")):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda):
+                raise ValueError("%s must be a CUDA tensor" % name)
+        if val.dtype not in (torch.float64, torch.float32):
+            raise ValueError("val must be float64 or float32")
+        if row_ptr.numel() != self.total_rows + self.n_sys or col.numel() != val.numel() \
+                or val.numel() != int(self.nnz_off[-1]):
+            raise ValueError("row_ptr needs sum(n_k) + n_sys entries and col, val nnz_off[-1] entries each")
         row_ptr = row_ptr.to(torch.int32).contiguous()
         col = col.to(torch.int32).contiguous()
         val = val.contiguous()
@@ -276,8 +304,10 @@ class BatchSolver:
     def solve(self, b: torch.Tensor, x: Optional[torch.Tensor] = None):
         """Returns (x, info dict with per-system numpy arrays)."""
         import numpy as np
+        _need_cuda(b, "b", numel=self.total_rows)
         if x is None:
             x = torch.zeros_like(b)
+        _need_cuda(x, "x", numel=self.total_rows)
         st = np.zeros(self.n_sys, np.int32)
         it = np.zeros(self.n_sys, np.int32)
         nr = np.zeros(self.n_sys, np.int32)
