@@ -6,7 +6,7 @@
  *
  * Problem statement (Section 1): solve A x = b for a sparse, non-singular
  * N x N matrix A, given b and an initial guess x0, with a preconditioner
- * M^{-1} (Algorithm 2, "p-bicgstab(A, M^{-1}, b, x0)"), a tolerance on the
+ * M^{-1} (the four inputs of Algorithm 2), a tolerance on the
  * recursively computed residual norm (Section 3.5) and a residual replacement
  * policy (Section 3.6, Eq. rr).
  *

@@ -26,7 +26,7 @@ R5  Stop: after iteration i, if ||r_{i+1}|| <= tol ||b||, the true residual
     converged; otherwise, with a replacement policy enabled a replacement is
     forced and the iteration continues, and without one the solve returns
     STAGNATED.  b = 0 returns x = 0 after 0 iterations.
-R6  Replacement placement ("after line 20"): r_{i+1}, k_{i+1}, w_{i+1} are
+R6  Replacement placement (right after the w update): r_{i+1}, k_{i+1}, w_{i+1} are
     recomputed from x_{i+1}, and s_i, l_i, z_i from g_i, before the second
     global reduction; n_i and v_i are kept.
 R7  Periodic policy: replace in iteration i when i > 0, i mod P == 0 and
@@ -36,7 +36,7 @@ R8  Mixed mode adds a relative trigger: replace when ||r_i|| <= theta * (the
 R15 Breakdown: a zero or non-finite alpha denominator, omega, (r_hat, r_i) or
     beta returns BREAKDOWN with the last finite x.  (y, y) == 0 sets omega = 0
     (y = 0 only when q = 0 in exact arithmetic), so the stop test decides.
-    With max_restarts > 0 (not in the paper) a breakdown instead restarts lines 2-3
+    With max_restarts > 0 (not in the paper) a breakdown instead restarts the initialisation
     from the current iterate, with the new residual as the shadow vector; the
     iteration in which the breakdown was found counts as completed.
 
@@ -128,7 +128,7 @@ def bicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float =
     bnorm = float(np.linalg.norm(b))
     if bnorm == 0.0:
         return SolveResult(np.zeros(n), Status.OK, 0, 0, 0.0, 0.0)
-    r = b - A64 @ x                     # line 2
+    r = b - A64 @ x                     # r_0
     p = r.copy()
     rhat = r.copy()
     rho = _dot(rhat, r)
@@ -138,25 +138,25 @@ def bicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float =
         res.status, res.rel_res_recursive, res.rel_res_true = Status.OK, rn / bnorm, rn / bnorm
         return res
     for i in range(maxit):
-        g = M.apply(p)                  # line 4
-        s = A64 @ g                     # line 5
-        sig = _dot(rhat, s)             # line 6
-        alpha = rho / sig if sig != 0.0 else math.inf   # line 7
+        g = M.apply(p)                  # g_i = M^{-1} p_i
+        s = A64 @ g                     # s_i = A g_i
+        sig = _dot(rhat, s)             # (r_0, s_i)
+        alpha = rho / sig if sig != 0.0 else math.inf   # alpha_i
         if sig == 0.0 or not math.isfinite(alpha):
             res.status = Status.BREAKDOWN
             break
-        q = r - alpha * s               # line 8
-        u = M.apply(q)                  # line 9
-        y = A64 @ u                     # line 10
-        qy, yy = _dot(q, y), _dot(y, y)  # line 11
-        omega = 0.0 if yy == 0.0 else qy / yy  # line 12
+        q = r - alpha * s               # q_i
+        u = M.apply(q)                  # u_i = M^{-1} q_i
+        y = A64 @ u                     # y_i = A u_i
+        qy, yy = _dot(q, y), _dot(y, y)  # (q_i, y_i), (y_i, y_i)
+        omega = 0.0 if yy == 0.0 else qy / yy  # omega_i
         if not math.isfinite(omega):
             res.status = Status.BREAKDOWN
             break
         x_old, r_old = x, r
-        x = (x + alpha * g) + omega * u  # line 13
-        r = q - omega * y                # line 14
-        rho_new = _dot(rhat, r)          # line 15
+        x = (x + alpha * g) + omega * u  # x_{i+1}
+        r = q - omega * y                # r_{i+1}
+        rho_new = _dot(rhat, r)          # (r_0, r_{i+1})
         rr = _dot(r, r)
         res.iterations = i + 1
         res.alpha.append(alpha)
@@ -176,12 +176,12 @@ def bicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float =
         if omega == 0.0 or rho == 0.0:
             res.status = Status.BREAKDOWN
             break
-        beta = (alpha / omega) * (rho_new / rho)   # line 16
+        beta = (alpha / omega) * (rho_new / rho)   # beta_i
         if not math.isfinite(beta):
             res.status = Status.BREAKDOWN
             break
         res.beta.append(beta)
-        p = r + beta * (p - omega * s)   # line 17
+        p = r + beta * (p - omega * s)   # p_{i+1}
         rho = rho_new
     res.x = x
     res.rel_res_recursive = math.sqrt(_dot(r, r)) / bnorm
@@ -206,7 +206,7 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
     With any policy enabled, reading R5's forced replacement is also active.
     ``track_bound`` computes f^r (history ``fr``) without acting on it.
     ``observer(stage, i, vectors)`` is called with stage "init", "iter" (after
-    l.20, before any replacement) and "replace" (after Eq. (rr)).
+    the w update, before any replacement) and "replace" (after Eq. (rr)).
     """
     A64 = _as_scipy(A)
     n = A64.shape[0]
@@ -231,7 +231,7 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
     tau = math.sqrt(eps) if rr_tau is None else rr_tau
     fbound = _GapBound(A64, M, b, eps, mixed) if (rr_auto or track_bound) else None
     while True:                             # restarts after breakdowns (max_restarts)
-        # l.2-3: initialisation
+        # initialisation of Algorithm 2
         r = (b - A64 @ x).astype(T)
         rhat = r.copy()
         k = M.apply(r)
@@ -280,17 +280,17 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
             i = it
             a_, b_, wp_ = sc(alpha), sc(beta), sc(omega_prev)
             g_prev, l_prev, s_prev, z_prev, n_prev, v_prev = g, l, s, z, nv, v
-            g = k + b_ * (g - wp_ * l)          # l.5
-            s = w + b_ * (s - wp_ * z)          # l.6
-            l = m + b_ * (l - wp_ * nv)         # l.7
-            z = t + b_ * (z - wp_ * v)          # l.8
-            q = r - a_ * s                      # l.9
-            u = k - a_ * l                      # l.10
-            y = w - a_ * z                      # l.11
-            qy, yy = _dot(q, y), _dot(y, y)     # l.12
-            nv = M.apply(z)                     # l.13
-            v = AT @ nv                         # l.14
-            omega = 0.0 if yy == 0.0 else qy / yy   # l.16
+            g = k + b_ * (g - wp_ * l)          # g_i
+            s = w + b_ * (s - wp_ * z)          # s_i
+            l = m + b_ * (l - wp_ * nv)         # l_i
+            z = t + b_ * (z - wp_ * v)          # z_i
+            q = r - a_ * s                      # q_i
+            u = k - a_ * l                      # u_i
+            y = w - a_ * z                      # y_i
+            qy, yy = _dot(q, y), _dot(y, y)     # first global reduction
+            nv = M.apply(z)                     # n_i = M^{-1} z_i
+            v = AT @ nv                         # v_i = A n_i
+            omega = 0.0 if yy == 0.0 else qy / yy   # omega_i
             if not math.isfinite(omega):
                 if n_restarts < max_restarts:
                     n_restarts += 1
@@ -309,10 +309,10 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
             if rr_auto and len(fr_hist) >= 2 and (fr_hist[-2] <= tau * rn_hist[-2] and fr_hist[-1] > tau * rn_hist[-1]):
                 do_rr = True                                             # Eq. (criterion)
             x_old = x
-            x = (x + alpha * g.astype(np.float64)) + omega * u.astype(np.float64)   # l.17
-            r_new = q - o_ * y                  # l.18
-            k_new = u - o_ * (m - a_ * nv)      # l.19
-            w_new = y - o_ * (t - a_ * v)       # l.20
+            x = (x + alpha * g.astype(np.float64)) + omega * u.astype(np.float64)   # x_{i+1}
+            r_new = q - o_ * y                  # r_{i+1}
+            k_new = u - o_ * (m - a_ * nv)      # k_{i+1}
+            w_new = y - o_ * (t - a_ * v)       # w_{i+1}
             if observer is not None:
                 observer("iter", i, dict(x=x_old, x_new=x, r=r, k=k, w=w, g=g, s=s, l=l, z=z, q=q, u=u,
                                          y=y, m=m, t=t, n=nv, v=v, r_new=r_new, k_new=k_new,
@@ -322,18 +322,18 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
             if fbound is not None:
                 fbound.step(alpha, beta, omega, omega_prev, x_old, r, k, w, g, s, l, z, q, u, y, m, t, nv, v)
             r, k, w = r_new, k_new, w_new
-            if do_rr:                           # Eq. (rr), after l.20 (reading R6)
+            if do_rr:                           # Eq. (rr), right after the w update (reading R6)
                 r, k, w, s, l, z = replace(x, g)
                 res.n_replacements += 1
                 if observer is not None:
                     observer("replace", i, dict(x=x, r=r, k=k, w=w, g=g, s=s, l=l, z=z))
                 if fbound is not None:
                     fbound.reset(x, k, g, s, l, z)
-            # l.21-24: second global reduction, overlapped with m = M^{-1} w, t = A m
+            # second global reduction, overlapped with m = M^{-1} w, t = A m
             rho_new, rw, rs, rz = _dot(rhat, r), _dot(rhat, w), _dot(rhat, s), _dot(rhat, z)
             rr = _dot(r, r)
-            m = M.apply(w)                      # l.22
-            t = AT @ m                          # l.23
+            m = M.apply(w)                      # m_{i+1}
+            t = AT @ m                          # t_{i+1}
             res.iterations = i + 1
             rn = math.sqrt(rr)
             if rn <= tol * bnorm:               # reading R5
@@ -371,8 +371,8 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
                     break
                 res.status = Status.BREAKDOWN
                 break
-            beta_new = (alpha / omega) * (rho_new / rho)                        # l.25
-            den = (rw + beta_new * rs) - (beta_new * omega) * rz                # l.26
+            beta_new = (alpha / omega) * (rho_new / rho)                        # beta_{i+1}
+            den = (rw + beta_new * rs) - (beta_new * omega) * rz                # alpha_{i+1} = rho_new / den
             alpha_new = rho_new / den if den != 0.0 else math.inf
             _log(res, alpha, omega, beta_new, rn, do_rr, x, i, record, fbound)
             if not (math.isfinite(beta_new) and den != 0.0 and math.isfinite(alpha_new)):

@@ -4,12 +4,13 @@
 // One launch runs the whole solve.  Rows are split into one contiguous chunk per
 // block.  Each iteration is two fused passes separated by grid barriers; each pass
 // is an SPMV fused with the AXPY recurrences and the partial dot products of one
-// global reduction phase, so the paper's "overlap GLRED with SPMV + PREC" becomes:
-// the reduction completes at the barrier the next SPMV needs anyway.
+// global reduction phase, so the paper's overlap of each global reduction with an SPMV
+// and a preconditioner application becomes: the reduction completes at the barrier
+// the next SPMV needs anyway.
 //
-//   pass A (lines 5-12 + 23 of iteration i-1): t_i = A m_i, then g, s, l, z, q, u, y
-//          and partials of (q,y), (y,y)
-//   pass B (lines 13-21): v_i = A n_i, omega_i, then x, r, k, w (q, u, y recomputed
+//   pass A: t_i = A m_i (the product the paper forms during the previous iteration's
+//          second reduction), then g, s, l, z, q, u, y and partials of (q,y), (y,y)
+//   pass B: v_i = A n_i, omega_i, then x, r, k, w (q, u, y recomputed
 //          bit-identically instead of stored) and partials of (r0,r_{i+1}),
 //          (r0,w_{i+1}), (r0,s_i), (r0,z_i), (r_{i+1},r_{i+1})
 //
@@ -455,10 +456,10 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   } while (0)
 
   // A breakdown (a zero or non-finite omega, (r0, r_i), beta or alpha denominator) can,
-  // if the options allow it, restart the method from the current iterate: lines 2-3
+  // if the options allow it, restart the method from the current iterate: the initialisation
   // again with x as the initial guess and the new r as the shadow vector.
   for (;;) {
-  // ---------------- initialisation (Algorithm 2, lines 2-3)
+  // ---------------- initialisation of Algorithm 2
   {
     Acc a_rr;
     DAcc a_bb, a_xx;
@@ -538,7 +539,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   for (; it < p.max_it; ++it) {
     // ---------------- m_i = M^{-1} w_i (Neumann only; on the fly otherwise)
     if (neu && !neumann_apply(p, team, p.w, p.m, (const T*)nullptr, (T*)nullptr)) return;
-    // ---------------- pass A: t_i = A m_i; lines 5-11; partials of line 12
+    // ---------------- pass A: t_i = A m_i; g, s, l, z, q, u, y; partials of (q, y), (y, y)
     const bool split = team.lanes > 1 && !neu && p.At.fmt == 0;   // lane-split SpMVs (batched CSR)
     if (split) spmv_lanes(team, p.At, p.w, p.t);
     {
@@ -596,7 +597,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       if (AUTO) team.template combine<14>(0, t14);
       else team.template combine<2>(0, *reinterpret_cast<double(*)[2]>(t14));
       PBCG_BCAST_BEGIN
-        sc[0] = t14[1] == 0.0 ? 0.0 : t14[0] / t14[1];   // line 16
+        sc[0] = t14[1] == 0.0 ? 0.0 : t14[0] / t14[1];   // omega_i
         if (AUTO) {
           for (int j = 1; j <= 12; ++j) gnorm[j] = sqrt(t14[j + 1]);   // r..t of iteration i
           sc[1] = gb_criterion(gb, p.rr_tau) ? 1.0 : 0.0;               // Eq. (criterion)
@@ -614,7 +615,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     if (p.rr_period > 0 && it > 0 && it % p.rr_period == 0 && rn >= rr_cutoff) do_rr = true;
     if (p.rr_theta > 0.0 && rn <= rr_theta_thr) do_rr = true;
     if (do_auto) do_rr = true;
-    // ---------------- pass B: v_i = A n_i; lines 17-20; partials of line 21
+    // ---------------- pass B: v_i = A n_i; x, r, k, w; partials of the second reduction
     if (split) spmv_lanes(team, p.At, p.z, p.v);
     {
       const T aT = T(alpha), oT = T(omega);
@@ -643,7 +644,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         const T y = fma(-aT, zi, wi);
         const double xo = p.x[i];
         if (AUTO) { a_xn.add(xo, xo); a_nn.add(ni, ni); a_vn.add(vi, vi); }
-        const double xn = fma(ox, (double)u, fma(ax, (double)gg, xo));  // line 17
+        const double xn = fma(ox, (double)u, fma(ax, (double)gg, xo));  // x_{i+1}
         const T rn1 = fma(-oT, y, q);                    // r_{i+1} = q_i - omega_i y_i
         const T kn = fma(-oT, fma(-aT, ni, mi), u);      // k_{i+1} = u_i - omega_i (m_i - alpha_i n_i)
         const T wn = fma(-oT, fma(-aT, vi, ti), y);      // w_{i+1} = y_i - omega_i (t_i - alpha_i v_i)
@@ -663,7 +664,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         team.template publish<3>(v3, 3);
       }
     }
-    // ---------------- residual replacement, Eq. (rr), after line 20 (reading R6)
+    // ---------------- residual replacement, Eq. (rr), right after the w update (reading R6)
     if (do_rr) {
       PBCG_SYNC();
       replace_r1<AUTO, SCALAR>(p, team, true);
@@ -673,7 +674,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     }
     rep_last = do_rr;
     PBCG_SYNC();
-    // ---------------- lines 21-26: second reduction, stopping test, beta, alpha
+    // ---------------- second reduction, stopping test, beta_{i+1}, alpha_{i+1}
     double t5[6];
     if (AUTO && do_rr) team.template combine<6>(1, t5);
     else team.template combine<5>(1, *reinterpret_cast<double(*)[5]>(t5));
@@ -738,8 +739,8 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     PBCG_BCAST_BEGIN
       if (AUTO) gb_end_iteration(gb, rn);
       if (do_rr) sc[3] = p.rr_theta * rn;
-      sc[0] = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_new, rho));                               // line 25
-      sc[1] = __dsub_rn(__dadd_rn(rw, __dmul_rn(sc[0], rs)), __dmul_rn(__dmul_rn(sc[0], omega), rz));   // line 26
+      sc[0] = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_new, rho));                               // beta_{i+1}
+      sc[1] = __dsub_rn(__dadd_rn(rw, __dmul_rn(sc[0], rs)), __dmul_rn(__dmul_rn(sc[0], omega), rz));   // its alpha denominator
       sc[2] = sc[1] != 0.0 ? __ddiv_rn(rho_new, sc[1]) : INFINITY;
     PBCG_BCAST_END
     beta_new = sc[0];
@@ -854,9 +855,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pbicgstab_multi_kernel(const S
 // ---------------------------------------------------------------------------
 // Classic preconditioned BiCGStab (Algorithm 1), the paper's reference method, with
 // the same team machinery.  Three grid barriers per iteration, one per global
-// reduction phase of Algorithm 1 (lines 6, 11, 15).  The new search direction
-// p_{i} = r_i + beta (p_{i-1} - omega s_{i-1}) (line 17) and q_i = r_i - alpha s_i
-// (line 8) are formed on the fly wherever the SpMV gathers them, so they need no pass of
+// reduction phase of Algorithm 1 ((r0, s_i); (q_i, y_i) with (y_i, y_i); (r0, r_{i+1})).
+// The new search direction p_{i} = r_i + beta (p_{i-1} - omega s_{i-1}) and
+// q_i = r_i - alpha s_i are formed on the fly wherever the SpMV gathers them, so they need no pass of
 // their own; p and s are double-buffered because a pass reads the old values at
 // neighbouring rows while writing the new ones.  No preconditioner or Jacobi (folded
 // into A D^{-1}: s = A g = (A D^{-1}) p, y = A u = (A D^{-1}) q); no replacement.
@@ -882,7 +883,7 @@ __device__ void classic_body(const SolverParams<T, VR>& p, Team& team) {
     }                                                                                    \
     return;                                                                              \
   } while (0)
-  // line 2: r_0 = b - A x_0; p_0 = r_0 (formed on the fly below, with beta = 0)
+  // r_0 = b - A x_0; p_0 = r_0 (formed on the fly below, with beta = 0)
   {
     Acc a_rr;
     DAcc a_bb;
@@ -925,7 +926,7 @@ __device__ void classic_body(const SolverParams<T, VR>& p, Team& team) {
     const T* s_old = sbuf[cur];
     T* p_new = pbuf[cur ^ 1];
     T* s_new = sbuf[cur ^ 1];
-    // lines 4-6: p_i (line 17 of the previous iteration), g_i = M^{-1} p_i, s_i = A g_i, (r0, s_i)
+    // p_i (from the previous iteration), g_i = M^{-1} p_i, s_i = A g_i, (r0, s_i)
     {
       const T bT = T(beta), oT = T(omega);
       Acc a_rs;
@@ -944,13 +945,13 @@ __device__ void classic_body(const SolverParams<T, VR>& p, Team& team) {
     {
       double t1[1];
       team.template combine<1>(0, t1);
-      if (threadIdx.x == 0) sc[0] = t1[0] != 0.0 ? rho / t1[0] : INFINITY;   // line 7
+      if (threadIdx.x == 0) sc[0] = t1[0] != 0.0 ? rho / t1[0] : INFINITY;   // alpha_i
       __syncthreads();
       alpha = sc[0];
       __syncthreads();
       if (!isfinite(alpha)) CL_FINISH(kBreakdown, it, rn);
     }
-    // lines 8-11: q_i = r_i - alpha s_i, u_i = M^{-1} q_i, y_i = A u_i, (q_i, y_i), (y_i, y_i)
+    // q_i = r_i - alpha s_i, u_i = M^{-1} q_i, y_i = A u_i, (q_i, y_i), (y_i, y_i)
     {
       const T aT = T(alpha);
       Acc a_qy, a_yy;
@@ -968,13 +969,13 @@ __device__ void classic_body(const SolverParams<T, VR>& p, Team& team) {
     {
       double t2[2];
       team.template combine<2>(1, t2);
-      if (threadIdx.x == 0) sc[0] = t2[1] == 0.0 ? 0.0 : t2[0] / t2[1];   // line 12
+      if (threadIdx.x == 0) sc[0] = t2[1] == 0.0 ? 0.0 : t2[0] / t2[1];   // omega_i
       __syncthreads();
       omega = sc[0];
       __syncthreads();
       if (!isfinite(omega)) CL_FINISH(kBreakdown, it, rn);
     }
-    // lines 13-15: x_{i+1} = (x_i + alpha g_i) + omega u_i, r_{i+1} = q_i - omega y_i, (r0, r_{i+1})
+    // x_{i+1} = (x_i + alpha g_i) + omega u_i, r_{i+1} = q_i - omega y_i, (r0, r_{i+1})
     {
       const T aT = T(alpha), oT = T(omega);
       const double ax = SCALAR ? alpha * p.dinv_x : alpha;   // x update (see minv_local)
@@ -1004,7 +1005,7 @@ __device__ void classic_body(const SolverParams<T, VR>& p, Team& team) {
       rho_new = t2[0];
       if (threadIdx.x == 0) {
         sc[0] = sqrt(t2[1]);
-        sc[1] = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_new, rho));   // line 16
+        sc[1] = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_new, rho));   // beta_i
       }
       __syncthreads();
       rn = sc[0];

@@ -38,16 +38,16 @@ PIPELINED = [
     ("q: s -> z", "q = r - a_ * s ", "q = r - a_ * z "),
     ("u: l -> s", "u = k - a_ * l ", "u = k - a_ * s "),
     ("y: z -> s", "y = w - a_ * z ", "y = w - a_ * s "),
-    ("omega: (y,y) -> (q,q)", "qy, yy = _dot(q, y), _dot(y, y)     # l.12", "qy, yy = _dot(q, y), _dot(q, q)     # l.12"),
-    ("n: M z -> M s", "nv = M.apply(z)                     # l.13", "nv = M.apply(s)                     # l.13"),
-    ("v: A n -> A z", "v = AT @ nv                         # l.14", "v = AT @ z                          # l.14"),
-    ("x: u -> q", "+ omega * u.astype(np.float64)   # l.17", "+ omega * q.astype(np.float64)   # l.17"),
+    ("omega: (y,y) -> (q,q)", "qy, yy = _dot(q, y), _dot(y, y)     # first", "qy, yy = _dot(q, y), _dot(q, q)     # first"),
+    ("n: M z -> M s", "nv = M.apply(z) ", "nv = M.apply(s) "),
+    ("v: A n -> A z", "v = AT @ nv ", "v = AT @ z "),
+    ("x: u -> q", "+ omega * u.astype(np.float64)", "+ omega * q.astype(np.float64)"),
     ("x: alpha g -> alpha k", "x = (x + alpha * g.astype(np.float64))", "x = (x + alpha * k.astype(np.float64))"),
     ("r: sign", "r_new = q - o_ * y ", "r_new = q + o_ * y "),
     ("k: n -> v", "k_new = u - o_ * (m - a_ * nv)", "k_new = u - o_ * (m - a_ * v)"),
     ("w: v -> n", "w_new = y - o_ * (t - a_ * v)", "w_new = y - o_ * (t - a_ * nv)"),
-    ("m: M w -> M r", "m = M.apply(w)                      # l.22", "m = M.apply(r)                      # l.22"),
-    ("t: A m -> A w", "t = AT @ m                          # l.23", "t = AT @ w                          # l.23"),
+    ("m: M w -> M r", "m = M.apply(w)                      # m_{i+1}", "m = M.apply(r)                      # m_{i+1}"),
+    ("t: A m -> A w", "t = AT @ m                          # t_{i+1}", "t = AT @ w                          # t_{i+1}"),
     ("(r0,s) <-> (r0,z)", "_dot(rhat, w), _dot(rhat, s), _dot(rhat, z)\n            rr",
      "_dot(rhat, w), _dot(rhat, z), _dot(rhat, s)\n            rr"),
     ("beta: alpha/omega inverted", "beta_new = (alpha / omega) * (rho_new / rho)", "beta_new = (omega / alpha) * (rho_new / rho)"),
@@ -66,13 +66,13 @@ PIPELINED = [
 ]
 
 CLASSIC = [
-    ("Alg. 1 line 5: A g -> A p", "s = A64 @ g                     # line 5", "s = A64 @ p                     # line 5"),
-    ("Alg. 1 line 8: sign", "q = r - alpha * s               # line 8", "q = r + alpha * s               # line 8"),
-    ("Alg. 1 line 12: (q,y)/(y,y) -> (q,y)/(q,q)", "qy, yy = _dot(q, y), _dot(y, y)  # line 11",
-     "qy, yy = _dot(q, y), _dot(q, q)  # line 11"),
-    ("Alg. 1 line 13: u -> q", "x = (x + alpha * g) + omega * u  # line 13", "x = (x + alpha * g) + omega * q  # line 13"),
-    ("Alg. 1 line 16: rho index", "beta = (alpha / omega) * (rho_new / rho)", "beta = (alpha / omega) * (rho / rho_new)"),
-    ("Alg. 1 line 17: s -> y", "p = r + beta * (p - omega * s)", "p = r + beta * (p - omega * y)"),
+    ("Alg. 1: s = A g -> A p", "s = A64 @ g ", "s = A64 @ p "),
+    ("Alg. 1: sign of alpha s in q", "q = r - alpha * s ", "q = r + alpha * s "),
+    ("Alg. 1: omega = (q,y)/(y,y) -> (q,y)/(q,q)", "qy, yy = _dot(q, y), _dot(y, y)  #",
+     "qy, yy = _dot(q, y), _dot(q, q)  #"),
+    ("Alg. 1: x update u -> q", "x = (x + alpha * g) + omega * u ", "x = (x + alpha * g) + omega * q "),
+    ("Alg. 1: beta with the rho ratio inverted", "beta = (alpha / omega) * (rho_new / rho)", "beta = (alpha / omega) * (rho / rho_new)"),
+    ("Alg. 1: p update s -> y", "p = r + beta * (p - omega * s)", "p = r + beta * (p - omega * y)"),
 ]
 
 

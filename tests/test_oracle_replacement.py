@@ -81,7 +81,7 @@ def test_mixed_with_replacement_reaches_1e10():
 
 def test_restart_after_breakdown_keeps_attainable_accuracy():
     """Not in the paper (its breakdown handling is silent): with max_restarts a breakdown
-    restarts lines 2-3 of Algorithm 2 from the current iterate.  On TP2 pushed to an
+    restarts the initialisation of Algorithm 2 from the current iterate.  On TP2 pushed to an
     unreachable tolerance the plain iteration diverges after stagnating and breaks down;
     with restarts the true residual stays at the attainable level."""
     A, _ = tp.normalise(tp.tp2(200))
