@@ -17,7 +17,9 @@
  *  - "device" pointers are CUDA global-memory pointers of the current device;
  *    "host" pointers are ordinary CPU memory.  Streams are cudaStream_t passed
  *    as void* (NULL = the legacy default stream).
- *  - Sizes: n < 2^31 - 1 rows, nnz < 2^31 - 1 stored entries (int32 indices).
+ *  - Sizes: 1 <= n <= PBCG_MAX_ROWS = 2^30 rows per system, nnz < 2^31 - 1 stored
+ *    entries (int32 indices).  The row limit keeps every 32-bit row index the kernels
+ *    form (a row plus the grid's thread count, a row plus a diagonal offset) in range.
  *  - A context is bound to the stream given at creation; contexts are not
  *    thread-safe.  Work is stream-ordered; a call blocks the host only when it
  *    returns results in host memory (pbcg_result, host vectors).
@@ -30,6 +32,8 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+#define PBCG_MAX_ROWS 1073741824
 
 typedef enum pbcg_status {
   PBCG_OK = 0,             /* converged: ||r_i|| <= tol ||b|| and the true residual too   */
@@ -302,7 +306,7 @@ typedef struct pbcg_batch_ctx pbcg_batch_ctx;
  * PBCG_PIPELINED only, cluster_blocks, lanes_per_row, batch_build; grid_blocks /
  * block_threads = 0 request the autotuner (it times the candidate launch shapes on
  * the first solve and keeps the fastest).  History options are ignored.  Errors:
- * INVALID_ARG (NULL, n_sys < 1, a system of size 0 or >= 2^31-1, decreasing
+ * INVALID_ARG (NULL, n_sys < 1, a system of size 0 or above PBCG_MAX_ROWS, decreasing
  * offsets, an invalid matrix found by the device validation, an option out of
  * range), OUT_OF_MEMORY, CUDA_ERROR; *out is NULL then. */
 pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_batch* batch,

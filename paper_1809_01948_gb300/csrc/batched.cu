@@ -524,7 +524,7 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
   if (B->row_off[0] != 0 || B->nnz_off[0] != 0) return set_error(PBCG_INVALID_ARG, "offsets must start at 0");
   for (int k = 0; k < ns; ++k) {
     const long long nk = B->row_off[k + 1] - B->row_off[k];
-    if (nk < 1 || nk >= 2147483647LL) return set_error(PBCG_INVALID_ARG, "system %d has an invalid size", k);
+    if (nk < 1 || nk > PBCG_MAX_ROWS) return set_error(PBCG_INVALID_ARG, "system %d has an invalid size", k);
     if (B->nnz_off[k + 1] < B->nnz_off[k]) return set_error(PBCG_INVALID_ARG, "nnz offsets must not decrease");
   }
   pbcg_batch_ctx* c = new (std::nothrow) pbcg_batch_ctx();

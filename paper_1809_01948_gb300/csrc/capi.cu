@@ -547,7 +547,7 @@ extern "C" pbcg_status pbicgstab_create(pbcg_ctx** out, const pbcg_matrix* A, co
                                         const pbcg_options* opt, void* stream) {
   if (!out || !A || !M || !opt) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_create");
   *out = nullptr;
-  if (A->n <= 0 || A->n >= 2147483647LL) return set_error(PBCG_INVALID_ARG, "n must be in [1, 2^31-2]");
+  if (A->n <= 0 || A->n > PBCG_MAX_ROWS) return set_error(PBCG_INVALID_ARG, "n must be in [1, 2^30]");
   if (A->format != PBCG_FMT_CSR && A->format != PBCG_FMT_DIA) return set_error(PBCG_INVALID_ARG, "unknown matrix format");
   if (A->val_dtype != PBCG_F64 && A->val_dtype != PBCG_F32) return set_error(PBCG_INVALID_ARG, "unknown value dtype");
   if (!A->val) return set_error(PBCG_INVALID_ARG, "matrix values are NULL");

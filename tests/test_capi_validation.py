@@ -52,7 +52,7 @@ def _create(lib, m, prec=capi.PREC_JACOBI, degree=0, **kw):
     return st, lib.pbicgstab_last_error().decode()
 
 
-@pytest.mark.parametrize("n", [0, -5, 2 ** 31 - 1, 2 ** 40])
+@pytest.mark.parametrize("n", [0, -5, 2 ** 30 + 1, 2 ** 31 - 1, 2 ** 40])
 def test_system_size_outside_int32_rows(lib, n):
     st, msg = _create(lib, _csr(n=n))
     assert st == INVALID and "n must be" in msg
