@@ -198,3 +198,39 @@ def test_pipelined_mutant_fails_a_pin(name, old, new):
 def test_classic_mutant_fails_a_pin(name, old, new):
     with np.errstate(all="ignore"):
         assert not _classic_pins_pass(_mutant(old, new)), name
+
+
+# ---------------------------------------------------------------- mixed-precision emulation
+MIXED = [
+    ("mixed: FP64 operator in the recurrences", "AT = A64.astype(T)", "AT = A64"),
+    ("mixed: preconditioner in FP64", "M = make_precond(precond, A64, degree, T)",
+     "M = make_precond(precond, A64, degree, np.float64)"),
+    ("mixed: replacement residual with FP32 values", "r_ = (b - A64 @ x_).astype(T)", "r_ = (b - AT @ x_).astype(T)"),
+    ("mixed: replacement s with FP32 values", "s_ = (A64 @ g_.astype(np.float64)).astype(T)", "s_ = (AT @ g_).astype(T)"),
+    ("mixed: x accumulated in FP32", "x = (x + alpha * g.astype(np.float64)) + omega * u.astype(np.float64)",
+     "x = ((x.astype(T) + a_ * g) + o_ * u).astype(np.float64)"),
+]
+
+
+def _mixed_pins_fail(monkeypatch, mod):
+    import oracle
+    import test_oracle_replacement as TR
+    monkeypatch.setattr(oracle, "pbicgstab", mod.pbicgstab)
+    failed = []
+    for fn in (TR.test_mixed_first_iterates_track_fp64, TR.test_mixed_with_replacement_reaches_1e10,
+               TR.test_mixed_emulation_keeps_vectors_in_fp32):
+        try:
+            with np.errstate(all="ignore"):
+                fn()
+        except (AssertionError, FloatingPointError, ValueError):
+            failed.append(fn.__name__)
+    return failed
+
+
+def test_unmutated_mixed_emulation_passes(monkeypatch):
+    assert _mixed_pins_fail(monkeypatch, _load(SOURCE)) == []
+
+
+@pytest.mark.parametrize("name,old,new", MIXED, ids=[m[0] for m in MIXED])
+def test_mixed_mutant_fails_a_pin(monkeypatch, name, old, new):
+    assert _mixed_pins_fail(monkeypatch, _mutant(old, new)), name

@@ -93,3 +93,42 @@ def test_restart_after_breakdown_keeps_attainable_accuracy():
     assert plain.status == oracle.Status.BREAKDOWN and plain.n_restarts == 0
     assert rs.n_restarts >= 1 and rs.status == oracle.Status.NOT_CONVERGED
     assert rs.rel_res_true <= 1e-10 < plain.rel_res_true
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_power_of_two_scaling_gives_identical_iterates(mixed):
+    """Metamorphic pin: with A -> 2^k A and b -> 2^k b every Jacobi-preconditioned
+    quantity of Algorithm 2 is either unchanged (k, g, u, l, m, n, alpha, omega, beta,
+    x) or scaled exactly by 2^k (r, w, s, z, q, y, t, v), in FP64 and in the FP32
+    emulation alike, so the iterates and the replacement schedule are bit-identical.
+    Applying M^{-1} to a wrong vector, or dropping it, breaks the equality."""
+    p = tp.problem_convdiff2d(24)
+    A = p.A.to_scipy()
+    kw = dict(precond="jacobi", tol=1e-30, maxit=60, rr_period=20, mixed=mixed, record=60)
+    r1 = oracle.pbicgstab(A, p.b, **kw)
+    r2 = oracle.pbicgstab(A * 4.0, p.b * 4.0, **kw)
+    assert r1.iterations == r2.iterations == 60
+    assert r1.replaced == r2.replaced and any(r1.replaced)
+    for a, b in zip(r1.xs, r2.xs):
+        assert np.array_equal(a, b)
+    assert np.array_equal(np.array(r1.alpha), np.array(r2.alpha))
+    assert np.array_equal(np.array(r1.rnorm) * 4.0, np.array(r2.rnorm))
+
+
+def test_mixed_emulation_keeps_vectors_in_fp32():
+    """The mixed mode's definition (FP32 values, vectors and preconditioner; FP64 x, dots,
+    scalars and replacement residual): every recurrence vector the oracle hands to its
+    observer is FP32, before and after replacements, and x stays FP64."""
+    p = tp.problem_convdiff2d(20)
+    A = p.A.to_scipy()
+    seen = []
+
+    def obs(stage, i, d):
+        for key, v in d.items():
+            if isinstance(v, np.ndarray):
+                want = np.float64 if key in ("x", "x_new") else np.float32
+                seen.append((stage, key, v.dtype == want))
+    r = oracle.pbicgstab(A, p.b, precond="jacobi", tol=1e-30, maxit=30, rr_period=10, mixed=True, observer=obs)
+    assert r.x.dtype == np.float64 and any(r.replaced)
+    assert seen and all(ok for _, _, ok in seen), [s for s in seen if not s[2]][:5]
+    assert {"init", "iter", "replace"} <= {s[0] for s in seen}
