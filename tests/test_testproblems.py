@@ -42,6 +42,14 @@ def test_tp2_upper_triangle_perturbed():
     assert D[5, 4] == -1.0 and D[5, 1] == -1.0
 
 
+def test_tp2_unsymmetric_positive_definite():
+    """Section 4 describes TP2 as positive definite but unsymmetric: x^T A x > 0 for
+    every x (its symmetric part is positive definite) while A != A^T."""
+    D = dense(tp.tp2(12, 1e-3))
+    assert not np.allclose(D, D.T)
+    assert np.linalg.eigvalsh((D + D.T) / 2).min() > 0.0
+
+
 @pytest.mark.parametrize("maker", [lambda: tp.poisson_2d(12), lambda: tp.upwind_2d(12), lambda: tp.upwind_3d(6)])
 def test_normalised_two_norm(maker):
     A, sigma = tp.normalise(maker())
@@ -92,7 +100,7 @@ def test_generators_deterministic():
         assert np.array_equal(s1.A.val, s2.A.val) and np.array_equal(s1.b, s2.b)
 
 
-def test_config_shapes():
+def test_workload_shapes():
     p = tp.problem_poisson2d()
     assert p.A.n == 10000 and np.allclose(p.x_star, 1 / 100.0)
     assert np.allclose(p.A.to_scipy() @ p.x_star, p.b)
