@@ -7,6 +7,13 @@ import torch
 import paper_1809_01948_gb300 as pb
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    """The checks run in the binding, but the constructors load the library first."""
+    from paper_1809_01948_gb300._build import build
+    build()
+
+
 def _bare_solver(n=8):
     s = pb.Solver.__new__(pb.Solver)
     s.n, s.nnz, s.ctx = n, 20, None
