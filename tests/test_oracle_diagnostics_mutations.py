@@ -49,6 +49,14 @@ MUTANTS = [
     ("bound u: ||k|| term dropped", 'd["u"] = (cur["k"] + 2 * a * cur["l"]) * eps', 'd["u"] = (2 * a * cur["l"]) * eps'),
 ]
 
+CLASSIC_MUTANTS = [
+    ("classic delta x: omega u dropped", "dx = L(\"x_new\") - (L(\"x\") + al * gex + om * uex)",
+     "dx = L(\"x_new\") - (L(\"x\") + al * gex)"),
+    ("classic delta r: sign", "dr = L(\"r_new\") - (L(\"q\") - om * A_(uex))", "dr = L(\"r_new\") - (L(\"q\") + om * A_(uex))"),
+    ("classic delta q: M p -> p", "dq = L(\"q\") - (L(\"r\") - al * A_(gex))", "dq = L(\"q\") - (L(\"r\") - al * A_(L(\"p\")))"),
+    ("classic superposition: A delta_x dropped", "self.sum = self.sum - (A_(dx) + dr + dq)", "self.sum = self.sum - (dr + dq)"),
+]
+
 PINS = [("local errors within bounds", T.test_local_errors_within_paper_bounds),
         ("gap recurrences", T.test_gap_recurrences_hold)]
 
@@ -86,3 +94,25 @@ def test_unmutated_source_passes(monkeypatch):
 def test_mutant_fails_a_pin(monkeypatch, name, old, new):
     assert SOURCE.count(old) == 1, "mutation site not unique or missing: %r" % old
     assert _failing_pins(monkeypatch, _load(SOURCE.replace(old, new))), name
+
+
+def _classic_pin_fails(monkeypatch, mod):
+    monkeypatch.setattr(T, "diagnostics", mod)
+    failed = []
+    for prec in ("none", "jacobi"):
+        try:
+            with np.errstate(all="ignore"):
+                T.test_classic_gap_is_superposition(prec)
+        except (AssertionError, FloatingPointError, ValueError):
+            failed.append(prec)
+    return failed
+
+
+def test_unmutated_classic_probe_passes(monkeypatch):
+    assert _classic_pin_fails(monkeypatch, _load(SOURCE)) == []
+
+
+@pytest.mark.parametrize("name,old,new", CLASSIC_MUTANTS, ids=[m[0] for m in CLASSIC_MUTANTS])
+def test_classic_probe_mutant_fails_the_superposition_pin(monkeypatch, name, old, new):
+    assert SOURCE.count(old) == 1, "mutation site not unique or missing: %r" % old
+    assert _classic_pin_fails(monkeypatch, _load(SOURCE.replace(old, new))), name
