@@ -639,6 +639,8 @@ static pbcg_status enqueue_solve(pbcg_ctx* c, const double* b, double* x) {
   int grid = 0, threads = 0;
   pbcg_status st = launch_shape(c, &grid, &threads);
   if (st != PBCG_OK) return st;
+  st = check_barrier_budget(c->opt.max_it, c->opt.max_restarts, c->degree, grid);
+  if (st != PBCG_OK) return st;
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->stream), "memset state");
   CK(cudaEventRecord(c->ev0, c->stream), "event record");
   if (c->precision == PBCG_MIXED) {

@@ -158,6 +158,20 @@ inline bool scalar_jacobi(const pbcg_ctx* c) {
   return c->prec_kind == PBCG_PREC_JACOBI && c->dconst && !c->opt.rr_auto;
 }
 
+// The grid barrier counts arrivals in 32 bits (barrier index x blocks).  An iteration
+// crosses at most 4d + 6 barriers (d = Neumann degree: two preconditioner applications,
+// passes A and B, a replacement and a failed stop test), a (re)start d + 2; keep the
+// solve's total times the blocks below 2^31 so the count cannot wrap.
+inline pbcg_status check_barrier_budget(int max_it, int max_restarts, int degree, int blocks) {
+  const long long per_it = 8 + 4LL * degree;
+  const long long starts = (4 + 2LL * degree) * ((long long)max_restarts + 1);
+  const long long budget = ((1LL << 31) - 1) / blocks;       // barriers the counter allows
+  if (((long long)max_it + 1) * per_it + starts > budget)
+    return pbcg::set_error(PBCG_INVALID_ARG, "max_it %d is too large for %d blocks per barrier (at most %lld)",
+                           max_it, blocks, (budget - starts) / per_it - 1);
+  return PBCG_OK;
+}
+
 inline double hot_bytes(const pbcg_ctx* c) {
   const double es = (double)elem_size(c->precision);
   double op;

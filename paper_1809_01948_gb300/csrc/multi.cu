@@ -160,7 +160,9 @@ extern "C" pbcg_status pbicgstab_solve_multi(pbcg_ctx* c, int32_t nrhs, const do
   // blocks per team: share the grid, at least 32 rows per block
   int bpt = std::max(1, G / teams);
   bpt = (int)std::min<long long>(bpt, std::max<long long>(1, (c->n + 31) / 32));
-  pbcg_status st = ensure_multi(c, teams, bpt);
+  pbcg_status st = check_barrier_budget(c->opt.max_it, c->opt.max_restarts, c->degree, bpt);
+  if (st != PBCG_OK) return st;
+  st = ensure_multi(c, teams, bpt);
   if (st != PBCG_OK) return st;
   float ms_total = 0.f;
   const size_t n = (size_t)c->n;

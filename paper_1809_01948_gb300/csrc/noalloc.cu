@@ -272,6 +272,10 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   int grid = opt->grid_blocks;
   if (grid == 0) grid = (int)std::min<long long>(std::max<long long>(1, (n + 31) / 32), std::min(max_co, 2 * sms));
   if (grid < 1 || grid > max_co) return set_error(PBCG_INVALID_ARG, "grid_blocks %d above %d", grid, max_co);
+  {
+    const pbcg_status bs = check_barrier_budget(opt->max_it, opt->max_restarts, 0, grid);
+    if (bs != PBCG_OK) return bs;
+  }
   SolverParams<double> p;
   memset(&p, 0, sizeof p);
   p.n = n;
