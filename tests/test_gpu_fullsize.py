@@ -3,6 +3,7 @@ options: automatic grid and block shape).
 
 2D: 1024 x 1024 convection-diffusion, 5 FP64 diagonals, Jacobi, tol 1e-10.
 3D: 256^3 convection-diffusion, CSR, Jacobi + Neumann degree 2, tol 1e-10.
+Batched: the 512 random banded systems, mixed precision, tol 1e-8.
 
 The oracle runs the first iterations at full size (each costs tens of milliseconds in 2D
 and a few seconds in 3D), so the first iterates are compared element-wise; for the whole
@@ -115,3 +116,38 @@ def test_convdiff2d_1024_automated_replacement_schedule(convdiff2d):
     rep_ref = [i for i, f in enumerate(ref.replaced) if f]
     assert len(rep_ref) >= 8
     assert rep_gpu[:8] == rep_ref[:8], (rep_gpu, rep_ref)
+
+
+def test_batched_512_systems_full_size():
+    """The batched workload at full size (512 random banded systems, 17.7M rows), with the
+    benchmark's options and autotuned launch: every system converges with its FP64 true
+    residual (recomputed here by the oracle's SpMV) below 1e-8, and on the largest, the
+    median and the smallest system the solution matches the oracle's mixed-precision
+    solve and the generating x* to 1e-6 (both solves stop at a 1e-8 true residual; these
+    diagonally dominant systems have condition numbers of order ten)."""
+    import torch
+    import paper_1809_01948_gb300 as pb
+    bp = tp.problem_batched_banded()
+    c = bp.concat()
+    dev = torch.device("cuda:0")
+    s = pb.BatchSolver(c["row_off"], c["nnz_off"], torch.from_numpy(c["row_ptr"]).to(dev),
+                       torch.from_numpy(c["col"]).to(dev), torch.from_numpy(c["val"]).to(dev), precond="jacobi",
+                       precision="mixed", tol=1e-8, max_it=1000, rr_theta=1e-3)
+    x, info = s.solve(torch.from_numpy(c["b"]).to(dev))
+    x = x.cpu().numpy()
+    s.close()
+    assert info["n_ok"] == 512 and np.all(info["status"] == 0)
+    assert np.max(info["rel_res_true"]) <= 1e-8 * (1 + 1e-12)   # OK means ||b - A x|| <= tol ||b||
+    sizes = np.diff(c["row_off"])
+    order = np.argsort(sizes)
+    for k, sysk in enumerate(bp.systems):
+        xk = x[c["row_off"][k]:c["row_off"][k + 1]]
+        assert _true_rel(sysk.A.to_scipy(np.float64), sysk.b, xk) <= 1.01e-8, k
+    for k in (order[-1], order[len(order) // 2], order[0]):
+        sysk = bp.systems[k]
+        xk = x[c["row_off"][k]:c["row_off"][k + 1]]
+        ref = oracle.pbicgstab(sysk.A.to_scipy(np.float64), sysk.b, precond="jacobi", tol=1e-8, maxit=1000,
+                               rr_theta=1e-3, mixed=True)
+        assert ref.status == oracle.Status.OK
+        assert np.linalg.norm(xk - ref.x) <= 1e-6 * np.linalg.norm(ref.x), k
+        assert np.linalg.norm(xk - sysk.x_star) <= 1e-6 * np.linalg.norm(sysk.x_star), k
