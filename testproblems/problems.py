@@ -1,7 +1,7 @@
 """Generators for the synthetic linear systems (see the package docstring)."""
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import Dict, List, Optional, Tuple
 
 import numpy as np

@@ -3,7 +3,6 @@ wrapping (check_barrier_budget, a host function): compiled with nvcc into a smal
 program linked against the library and run without a GPU.  It must accept every solve the
 benchmarks and tests run and refuse the first max_it past the limit it reports."""
 import os
-import shutil
 import subprocess
 import tempfile
 

@@ -4,7 +4,6 @@ max-over-ranks timing the benchmark reports."""
 import os
 import socket
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

@@ -1,7 +1,6 @@
 """Oracle pins for Algorithm 1 (classic preconditioned BiCGStab)."""
 import numpy as np
 import pytest
-import scipy.sparse as sp
 import scipy.sparse.linalg as spl
 
 import oracle
