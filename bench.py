@@ -387,7 +387,13 @@ def cpu_baseline(args, gpu_iterations: int, sample_iters: int = 40):
     return {"value": round(per_it * iters * 1e3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
             "sample": "%d iterations of the FP64 numpy oracle on the full 1024x1024 system (%.1f s), "
                       "extrapolated to %d iterations" % (s["iterations"], s["seconds"], iters),
-            "ms_per_iteration": round(per_it * 1e3, 3)}
+            "ms_per_iteration": round(per_it * 1e3, 3), "host": _host()}
+
+
+def _host():
+    """The machine the CPU baseline ran on (the oracle itself uses one thread)."""
+    import platform
+    return {"arch": platform.machine(), "logical_cpus": os.cpu_count()}
 
 
 # ----------------------------------------------------------------------------- batched and autograd
@@ -562,7 +568,7 @@ def run_reference(args):
                        "replacement": {"rr_period": 100}},
             "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle",
                              "sample": "%d iterations per step of the numpy oracle, extrapolated to %d iterations"
-                                       % (args.cpu_iters, iters)},
+                                       % (args.cpu_iters, iters), "host": _host()},
             "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
