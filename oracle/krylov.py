@@ -39,6 +39,21 @@ R15 Breakdown: a zero or non-finite alpha denominator, omega, (r_hat, r_i) or
     With max_restarts > 0 (not in the paper) a breakdown instead restarts the initialisation
     from the current iterate, with the new residual as the shadow vector; the
     iteration in which the breakdown was found counts as completed.
+R20 Periodic restart (not in the paper; for the FP32 recurrences of mixed mode):
+    with restart_period = P > 0, after every P completed iterations since the last
+    (re)start the method restarts its initialisation from the current iterate: r = b - A x
+    in FP64, the new r as the shadow vector, beta = 0 and zero g, s, l, z, n, v (reading
+    R3).  It bounds how long the auxiliary recurrences' rounding errors can grow and is an
+    FP64 outer correction around the inner FP32 iteration.  A failed R5 verification then
+    restarts instead of returning STAGNATED.  The stop test at every (re)start uses the
+    FP64 norm ||b - A x|| (identical to ||r_0|| in FP64 mode).
+R21 Progress-based stagnation (stag_window = W > 0; the second half of the stop rule
+    R5): at every (re)start the FP64 true residual is compared with a reference value;
+    when it is at most half of it, it becomes the new reference, and when W or more
+    iterations have passed since the reference was set without that, the solve returns
+    STAGNATED with the iterate of the smallest true residual seen at a (re)start.  At
+    max_it (NOT_CONVERGED) that iterate is also returned when its true residual is
+    smaller than the last iterate's.
 
 Mixed emulation (``mixed=True``): every vector except x and b is stored in
 FP32 and every vector operation is evaluated in FP32 with the FP32-rounded
@@ -196,7 +211,8 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
               maxit: int = 1000, rr_period: int = 0, rr_theta: float = 0.0, rr_auto: bool = False,
               rr_tau: Optional[float] = None, mixed: bool = False, record: int = 0,
               observer: Optional[Callable] = None, track_bound: bool = False,
-              max_restarts: int = 0) -> SolveResult:
+              max_restarts: int = 0, restart_period: int = 0, stag_window: int = 0,
+              contract: bool = False) -> SolveResult:
     """Algorithm 2 of the paper (lines cited as "l.N"), plus Eq. (rr) replacements.
 
     Replacement policies (any combination; all off means plain p-BiCGStab):
@@ -204,6 +220,12 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
       rr_theta  > 0      relative trigger, reading R8;
       rr_auto            Eq. (criterion) with tau = rr_tau (default sqrt(eps)).
     With any policy enabled, reading R5's forced replacement is also active.
+    restart_period = P > 0 restarts the method every P iterations (reading R20);
+    stag_window = W > 0 stops a solve that no longer makes progress (reading R21).
+    ``contract`` (mixed mode only) evaluates every FP32 operation a + s c of the
+    recurrences, and every FP32 row product, with one rounding, as a fused multiply-add
+    does (reading R11): another equally valid evaluation, used to measure how much the
+    FP32 iterates depend on the rounding of single operations.
     ``track_bound`` computes f^r (history ``fr``) without acting on it.
     ``observer(stage, i, vectors)`` is called with stage "init", "iter" (after
     the w update, before any replacement) and "replace" (after Eq. (rr)).
@@ -212,6 +234,9 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
     n = A64.shape[0]
     T = np.float32 if mixed else np.float64
     AT = A64.astype(T)
+    contract = contract and mixed
+    if contract:
+        AT = _OneRounding(AT)
     M = make_precond(precond, A64, degree, T)
     b = np.asarray(b, dtype=np.float64)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
@@ -224,15 +249,19 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
     sc = (lambda a: T(a))                     # scalar in the vector precision
 
     it = 0
-    n_restarts = 0
+    n_restarts = 0                          # breakdown restarts (bounded by max_restarts)
+    n_periodic = 0                          # periodic restarts (reading R20)
     first = True
     rn0 = 0.0
+    ref_true, ref_it = math.inf, 0          # reading R21
+    best_true, x_best = math.inf, None
     eps = EPS64
     tau = math.sqrt(eps) if rr_tau is None else rr_tau
     fbound = _GapBound(A64, M, b, eps, mixed) if (rr_auto or track_bound) else None
     while True:                             # restarts after breakdowns (max_restarts)
         # initialisation of Algorithm 2
-        r = (b - A64 @ x).astype(T)
+        r64 = b - A64 @ x
+        r = r64.astype(T)
         rhat = r.copy()
         k = M.apply(r)
         w = AT @ k
@@ -241,12 +270,26 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
         rho = _dot(rhat, r)
         rw = _dot(rhat, w)
         rn = math.sqrt(_dot(r, r))
+        rt = math.sqrt(_dot(r64, r64))      # FP64 ||b - A x|| (= rn in FP64 mode)
         if first:
             rn0 = rn
-        if rn <= tol * bnorm:
+        it_start = it
+        if rt <= tol * bnorm:
             res.status, res.rel_res_recursive = Status.OK, rn / bnorm
             res.x, res.rel_res_true, res.iterations = x, _true_res(A64, b, x) / bnorm, it
+            res.n_restarts = n_restarts + n_periodic
             return res
+        if stag_window > 0:                 # reading R21
+            if rt <= 0.5 * ref_true:
+                ref_true, ref_it = rt, it
+            elif it - ref_it >= stag_window:
+                res.status, res.rel_res_recursive = Status.STAGNATED, rn / bnorm
+                res.x = x_best if (x_best is not None and best_true < rt) else x
+                res.rel_res_true, res.iterations = _true_res(A64, b, res.x) / bnorm, it
+                res.n_restarts = n_restarts + n_periodic
+                return res
+            if rt < best_true:
+                best_true, x_best = rt, x.copy()
         alpha = rho / rw if rw != 0.0 else math.inf
         if rw == 0.0 or not math.isfinite(alpha):
             res.status = Status.BREAKDOWN
@@ -280,13 +323,22 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
             i = it
             a_, b_, wp_ = sc(alpha), sc(beta), sc(omega_prev)
             g_prev, l_prev, s_prev, z_prev, n_prev, v_prev = g, l, s, z, nv, v
-            g = k + b_ * (g - wp_ * l)          # g_i
-            s = w + b_ * (s - wp_ * z)          # s_i
-            l = m + b_ * (l - wp_ * nv)         # l_i
-            z = t + b_ * (z - wp_ * v)          # z_i
-            q = r - a_ * s                      # q_i
-            u = k - a_ * l                      # u_i
-            y = w - a_ * z                      # y_i
+            if not contract:
+                g = k + b_ * (g - wp_ * l)          # g_i
+                s = w + b_ * (s - wp_ * z)          # s_i
+                l = m + b_ * (l - wp_ * nv)         # l_i
+                z = t + b_ * (z - wp_ * v)          # z_i
+                q = r - a_ * s                      # q_i
+                u = k - a_ * l                      # u_i
+                y = w - a_ * z                      # y_i
+            else:                                   # the same with one rounding per a + s c
+                g = _fma(k, b_, _fma(g, -wp_, l))
+                s = _fma(w, b_, _fma(s, -wp_, z))
+                l = _fma(m, b_, _fma(l, -wp_, nv))
+                z = _fma(t, b_, _fma(z, -wp_, v))
+                q = _fma(r, -a_, s)
+                u = _fma(k, -a_, l)
+                y = _fma(w, -a_, z)
             qy, yy = _dot(q, y), _dot(y, y)     # first global reduction
             nv = M.apply(z)                     # n_i = M^{-1} z_i
             v = AT @ nv                         # v_i = A n_i
@@ -310,9 +362,14 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
                 do_rr = True                                             # Eq. (criterion)
             x_old = x
             x = (x + alpha * g.astype(np.float64)) + omega * u.astype(np.float64)   # x_{i+1}
-            r_new = q - o_ * y                  # r_{i+1}
-            k_new = u - o_ * (m - a_ * nv)      # k_{i+1}
-            w_new = y - o_ * (t - a_ * v)       # w_{i+1}
+            if not contract:
+                r_new = q - o_ * y                  # r_{i+1}
+                k_new = u - o_ * (m - a_ * nv)      # k_{i+1}
+                w_new = y - o_ * (t - a_ * v)       # w_{i+1}
+            else:
+                r_new = _fma(q, -o_, y)
+                k_new = _fma(u, -o_, _fma(m, -a_, nv))
+                w_new = _fma(y, -o_, _fma(t, -a_, v))
             if observer is not None:
                 observer("iter", i, dict(x=x_old, x_new=x, r=r, k=k, w=w, g=g, s=s, l=l, z=z, q=q, u=u,
                                          y=y, m=m, t=t, n=nv, v=v, r_new=r_new, k_new=k_new,
@@ -343,8 +400,13 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
                     _log(res, alpha, omega, None, rn, do_rr, x, i, record, fbound)
                     break
                 if not any_rr:
-                    res.status = Status.STAGNATED
                     _log(res, alpha, omega, None, rn, do_rr, x, i, record, fbound)
+                    if restart_period > 0:          # reading R20: restart from x instead
+                        n_periodic += 1
+                        it += 1
+                        restart = True
+                        break
+                    res.status = Status.STAGNATED
                     break
                 r, k, w, s, l, z = replace(x, g)     # forced replacement
                 res.n_replacements += 1
@@ -385,13 +447,35 @@ def pbicgstab(A, b, x0=None, precond: str = "none", degree: int = 0, tol: float 
                 break
             alpha, beta, omega_prev, rho = alpha_new, beta_new, omega, rho_new
             it += 1
+            if restart_period > 0 and it - it_start >= restart_period:   # reading R20
+                n_periodic += 1
+                restart = True
+                break
         if not restart:
             break
-    res.n_restarts = n_restarts
+    res.n_restarts = n_restarts + n_periodic
+    if res.status == Status.NOT_CONVERGED and x_best is not None and best_true < _true_res(A64, b, x):
+        x = x_best                          # reading R21
     res.x = x
     res.rel_res_recursive = rn / bnorm
     res.rel_res_true = _true_res(A64, b, x) / bnorm
     return res
+
+
+def _fma(a, s, c):
+    """a + s c for FP32 vectors a, c and an FP32 scalar s, rounded once to FP32 (the FP32
+    product is exact in FP64; the FP64 sum is then rounded to FP32)."""
+    return (a.astype(np.float64) + np.float64(s) * c.astype(np.float64)).astype(np.float32)
+
+
+class _OneRounding:
+    """An FP32 matrix whose row products are accumulated in FP64 and rounded once to FP32."""
+
+    def __init__(self, A32):
+        self.A = A32.astype(np.float64)
+
+    def __matmul__(self, v):
+        return (self.A @ v.astype(np.float64)).astype(np.float32)
 
 
 def _log(res, alpha, omega, beta_new, rn, replaced, x, i, record, fbound):
