@@ -42,7 +42,8 @@ typedef enum pbcg_status {
   PBCG_OUT_OF_MEMORY = 3,  /* device allocation failed                                   */
   PBCG_NOT_CONVERGED = 4,  /* max_it iterations done without meeting the tolerance       */
   PBCG_BREAKDOWN = 5,      /* a zero or non-finite alpha denominator, omega, (r0,r_i)    */
-  PBCG_STAGNATED = 6,      /* recursive residual met tol, true residual did not, no replacement policy */
+  PBCG_STAGNATED = 6,      /* recursive residual met tol, true residual did not, no replacement
+                              or restart policy; or no progress (options.stag_window)     */
   PBCG_TIMEOUT = 7         /* a grid-wide wait inside a kernel exceeded timeout_ms       */
 } pbcg_status;
 
@@ -132,7 +133,11 @@ typedef struct pbcg_options {
   int32_t grid_blocks;     /* persistent grid size; 0 = automatic                     */
   int32_t block_threads;   /* threads per block, a multiple of 32 up to 1024, or up to
                               512 for a mixed solve whose working set exceeds L2
-                              (INVALID_ARG above); 0 = that maximum                     */
+                              (INVALID_ARG above); 0 = that maximum.  A system in stencil
+                              storage whose row count is a multiple of 4, solved with
+                              16-byte aligned b and x (and hist_x) by Algorithm 2 without
+                              rr_auto, runs kernels that take four rows per thread in the
+                              hot passes when block_threads is 0 (then 512) or <= 512   */
   int32_t max_restarts;    /* after a breakdown (zero or non-finite omega, (r0,r_i),
                               beta or alpha denominator) restart Algorithm 2 from the
                               current iterate with a new shadow vector, at most this many
@@ -154,6 +159,33 @@ typedef struct pbcg_options {
                               registers, up to six 256-thread or three 512-thread blocks
                               per SM; mixed precision, cluster_blocks 0, 2, 4 or 8,
                               block_threads 0 or <= 512); other values: INVALID_ARG     */
+  int32_t restart_period;  /* > 0: restart Algorithm 2 from the current iterate after every P
+                              iterations since the last (re)start -- r = b - A x in FP64, the
+                              new r as shadow vector, beta = 0 (not in the paper: an FP64
+                              outer correction that bounds how long the rounding errors of
+                              the auxiliary recurrences can grow, for mixed precision); a
+                              failed verification of the stop test then restarts instead of
+                              returning STAGNATED.  0 = off                              */
+  int32_t stag_window;     /* > 0: return PBCG_STAGNATED when the FP64 true residual, taken
+                              at every (re)start, has not halved for this many iterations;
+                              x is then the (re)start iterate with the smallest true
+                              residual (also at NOT_CONVERGED when it beats the last
+                              iterate).  Single-system solves keep that iterate; multi-RHS
+                              and batched solves return the last one.  0 = off           */
+  double rr_cutoff;        /* periodic replacement stops once ||r_i|| < rr_cutoff ||r_0||
+                              (Section 3.6); <= 0: sqrt(2^-52)                          */
+  int32_t prefetch_trips;  /* single-system solver: how many grid-wide row sweeps ahead each
+                              thread asks L2 for its operands (prefetch.global.L2, which
+                              holds no registers); 0 = automatic (1 for the one-row kernels
+                              of a stencil system whose working set exceeds L2, else off),
+                              < 0 = off, at most 16                                      */
+  int32_t barrier_overlap; /* single-system solver: > 0 = on where it applies, <= 0 = off.  Each block arrives at the grid barrier that ends a
+                              reduction phase, computes the next SPMV for the rows of its
+                              chunk whose operands are all its own rows, then waits: the
+                              on-chip form of overlapping a global reduction with the SPMV
+                              (Section 1).  Applies with the chunked row order (matrix
+                              bandwidth below half a chunk), no or Jacobi preconditioning,
+                              Algorithm 2 without rr_auto                               */
 } pbcg_options;
 
 typedef struct pbcg_result {
@@ -170,7 +202,8 @@ typedef struct pbcg_result {
 typedef struct pbcg_ctx pbcg_ctx;
 
 /* Fill *opt with defaults: FP64, max_it 10000, tol 1e-10, no replacement, no
- * restarts, timeout 2000 ms, no history, automatic launch shape.  opt: host, non-NULL. */
+ * restarts, no stagnation window, replacement cutoff sqrt(2^-52), timeout 2000 ms, no
+ * history, automatic launch shape.  opt: host, non-NULL. */
 pbcg_status pbicgstab_default_options(pbcg_options* opt);
 
 /* Create a solver context for A and M^{-1} (Algorithm 2's inputs other than b,
@@ -247,6 +280,29 @@ pbcg_status pbicgstab_csr_value_grad(pbcg_ctx* ctx, int32_t nrhs, const double* 
  * n doubles, must not overlap).  Stream-ordered.  Errors: INVALID_ARG (NULL),
  * CUDA_ERROR. */
 pbcg_status pbicgstab_spmv(pbcg_ctx* ctx, const double* x, double* y);
+
+/* Work vectors of Algorithm 2 as the context's last single-system solve left them
+ * (pbicgstab_solve / pbicgstab_solve_host), for checking the state after a step: after
+ * an iteration i that ended with an Eq. (rr) replacement these are the replaced
+ * r_{i+1}, k_{i+1}, w_{i+1} and s_i, l_i, z_i (Section 3.6), with g_i and the shadow
+ * vector r0.  `which` selects one: */
+typedef enum pbcg_vector {
+  PBCG_VEC_R = 0, PBCG_VEC_RHAT = 1, PBCG_VEC_K = 2, PBCG_VEC_W = 3, PBCG_VEC_G = 4,
+  PBCG_VEC_S = 5, PBCG_VEC_L = 6, PBCG_VEC_Z = 7
+} pbcg_vector;
+/* dst: device, n doubles (the stored vector widened to FP64; with the scaled-form
+ * Jacobi of a constant diagonal, k, g and l are returned unscaled, i.e. as M^{-1} r,
+ * M^{-1} p and M^{-1} s).  Stream-ordered.  Errors: INVALID_ARG (NULL, unknown
+ * `which`), CUDA_ERROR. */
+pbcg_status pbicgstab_get_vector(pbcg_ctx* ctx, int32_t which, double* dst);
+
+/* The launch of the context's last single-system solve: info[0] grid blocks, info[1]
+ * threads per block, info[2] rows per thread in the hot passes (1, or 4 for the four-row
+ * kernels of the stencil storage), info[3] the L2 prefetch distance in row sweeps (0 =
+ * off) plus 256 when the barriers overlap the interior SPMV rows (options.barrier_overlap).
+ * All zero before the first solve.  ctx, info: host, non-NULL.  Errors:
+ * INVALID_ARG (NULL). */
+pbcg_status pbicgstab_launch_info(const pbcg_ctx* ctx, int32_t info[4]);
 
 /* *rel = ||b - A x|| / ||b|| in FP64, the true relative residual whose gap to the
  * recursive residual Section 3 analyses (b, x: device; rel: host).  Waits.
@@ -360,12 +416,16 @@ pbcg_status pbicgstab_solve_batched(const pbcg_batch* batch, const pbcg_options*
  * b: device, read.  x: device, read as x0 and overwritten.  res: host, filled
  * (time_ms is -1: no events are created).  The call waits for the solve.
  *
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls on a device share the one array and it keeps
- * the last call's contents (the solver re-initialises what must start at zero):
- * calls that overlap on the GPU -- from several host threads or streams at
- * once -- race on it and must be serialised by the caller. */
+ * Every call looks up the array's device address (cudaGetSymbolAddress, which
+ * allocates nothing) in the current context; the call then validates A on the
+ * device and waits for that result, and waits for the solve at the end, so it
+ * synchronises `stream` twice.  With default options (block_threads and
+ * grid_blocks 0) it uses the launch shape pbicgstab_solve chooses for a context that
+ * keeps A as given (options.operator_storage PBCG_STORAGE_GENERAL).  All calls
+ * on a device share the one array and it keeps the last call's contents (the
+ * solver re-initialises what must start at zero): calls that overlap on the GPU --
+ * from several host threads or streams at once -- race on it and must be
+ * serialised by the caller. */
 #define PBCG_NOALLOC_MAX_N 32768
 #define PBCG_NOALLOC_MAX_VALUES 524288
 pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_precond* M, const pbcg_options* opt,

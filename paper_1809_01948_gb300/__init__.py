@@ -76,7 +76,9 @@ class Solver:
                  precision: str = "fp64", tol: float = 1e-10, max_it: int = 10000, rr_period: int = 0,
                  rr_theta: float = 0.0, timeout_ms: float = 2000.0, grid_blocks: int = 0,
                  block_threads: int = 0, max_restarts: int = 0, rr_auto: bool = False, rr_tau: float = 0.0,
-                 method: str = "pipelined", operator_storage: str = "auto", stream: Optional[torch.cuda.Stream] = None):
+                 method: str = "pipelined", operator_storage: str = "auto", restart_period: int = 0,
+                 stag_window: int = 0, rr_cutoff: float = 0.0, prefetch_trips: int = 0,
+                 barrier_overlap: int = 0, stream: Optional[torch.cuda.Stream] = None):
         lib = _lib()
         self.n = int(n)
         self.stream = stream
@@ -124,6 +126,11 @@ class Solver:
         self.opt.rr_tau = rr_tau
         self.opt.method = _METHOD[method]
         self.opt.operator_storage = _STORAGE[operator_storage]
+        self.opt.restart_period = restart_period
+        self.opt.stag_window = stag_window
+        self.opt.rr_cutoff = rr_cutoff
+        self.opt.prefetch_trips = prefetch_trips
+        self.opt.barrier_overlap = barrier_overlap
         self.ctx = C.c_void_p()
         _check(lib.pbicgstab_create(C.byref(self.ctx), C.byref(m), C.byref(p), C.byref(self.opt),
                                     _stream_handle(stream)), "pbicgstab_create")
@@ -230,6 +237,22 @@ class Solver:
         _check(_lib().pbicgstab_spmv(self.ctx, _ptr(x), _ptr(y)), "pbicgstab_spmv")
         return y
 
+    VECTORS = ("r", "rhat", "k", "w", "g", "s", "l", "z")
+
+    def launch_info(self) -> dict:
+        """The last solve's launch (``pbicgstab_launch_info``)."""
+        info = (C.c_int32 * 4)()
+        _check(_lib().pbicgstab_launch_info(self.ctx, info), "pbicgstab_launch_info")
+        return dict(grid_blocks=info[0], block_threads=info[1], rows_per_thread=info[2],
+                    prefetch_trips=info[3] % 256, barrier_overlap=info[3] // 256)
+
+    def get_vector(self, name: str) -> torch.Tensor:
+        """A work vector of the last solve (``pbicgstab_get_vector``) as a CUDA float64 tensor."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = torch.empty(self.n, dtype=torch.float64, device=dev)
+        _check(_lib().pbicgstab_get_vector(self.ctx, self.VECTORS.index(name), _ptr(out)), "pbicgstab_get_vector")
+        return out
+
     def true_residual(self, b: torch.Tensor, x: torch.Tensor) -> float:
         _need_cuda(b, "b", numel=self.n)
         _need_cuda(x, "x", numel=self.n)
@@ -262,7 +285,8 @@ class BatchSolver:
     def __init__(self, row_off, nnz_off, row_ptr, col, val, precond: str = "jacobi", precision: str = "mixed",
                  tol: float = 1e-8, max_it: int = 1000, rr_period: int = 0, rr_theta: float = 0.0,
                  grid_blocks: int = 0, block_threads: int = 0, max_restarts: int = 0, cluster_blocks: int = 0,
-                 lanes_per_row: int = 0, build: str = "auto", stream: Optional[torch.cuda.Stream] = None):
+                 lanes_per_row: int = 0, build: str = "auto", restart_period: int = 0, stag_window: int = 0,
+                 stream: Optional[torch.cuda.Stream] = None):
         import numpy as np
         lib = _lib()
         self.row_off = np.ascontiguousarray(row_off, dtype=np.int64)
@@ -297,6 +321,8 @@ class BatchSolver:
         self.opt.cluster_blocks = cluster_blocks
         self.opt.lanes_per_row = lanes_per_row
         self.opt.batch_build = _BATCH_BUILD[build]
+        self.opt.restart_period = restart_period
+        self.opt.stag_window = stag_window
         self.ctx = C.c_void_p()
         _check(lib.pbicgstab_batch_create(C.byref(self.ctx), C.byref(bt), C.byref(self.opt), _stream_handle(stream)),
                "pbicgstab_batch_create")

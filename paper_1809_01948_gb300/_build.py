@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libpbicgstab.so")
-SOURCES = ["capi.cu", "batched.cu", "noalloc.cu", "multi.cu", "propagation.cu", "stencil.cu"]
+SOURCES = ["capi.cu", "kernels_f64.cu", "kernels_f32.cu", "kernels_vec.cu", "batched.cu", "noalloc.cu", "multi.cu",
+           "propagation.cu", "stencil.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -41,7 +41,9 @@ class Options(C.Structure):
                 ("grid_blocks", C.c_int32), ("block_threads", C.c_int32),
                 ("max_restarts", C.c_int32), ("method", C.c_int32), ("rr_tau", C.c_double),
                 ("operator_storage", C.c_int32), ("cluster_blocks", C.c_int32),
-                ("lanes_per_row", C.c_int32), ("batch_build", C.c_int32)]
+                ("lanes_per_row", C.c_int32), ("batch_build", C.c_int32),
+                ("restart_period", C.c_int32), ("stag_window", C.c_int32), ("rr_cutoff", C.c_double),
+                ("prefetch_trips", C.c_int32), ("barrier_overlap", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -78,6 +80,8 @@ PROTOTYPES = {
     "pbicgstab_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Result)]),
     "pbicgstab_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "pbicgstab_true_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "pbicgstab_get_vector": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "pbicgstab_launch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "pbicgstab_destroy": (C.c_int, [C.c_void_p]),
     "pbicgstab_last_error": (C.c_char_p, []),
     "pbicgstab_test_barrier_timeout": (C.c_int, [C.c_double, C.c_int32, C.POINTER(C.c_int32)]),

@@ -40,6 +40,9 @@ struct BatchDev {
   int rr_period;
   double rr_theta;
   int max_restarts;
+  int restart_period;
+  int stag_window;
+  double rr_cutoff;
   int lanes;                  // threads per row in the SpMVs of passes A and B
 };
 
@@ -95,6 +98,13 @@ __device__ void build_params(const BatchDev& d, int k, SolverParams<T, VR>& p) {
   p.rr_theta = d.rr_theta;
   p.timeout_ns = 0;
   p.max_restarts = d.max_restarts;
+  p.restart_period = d.restart_period;
+  p.stag_window = d.stag_window;
+  p.xbest = nullptr;   // stagnation is detected per system, but the last iterate is returned
+  p.rr_cutoff = d.rr_cutoff;
+  p.strided = 0;
+  p.overlap = 0;   // block and cluster teams: no grid barrier to overlap
+  p.halo = 0;
 }
 
 template <typename T, typename VR>
@@ -355,6 +365,9 @@ static BatchDev make_dev(pbcg_batch_ctx* c, const double* b, double* x, int lane
   d.rr_period = c->opt.rr_period;
   d.rr_theta = c->opt.rr_theta;
   d.max_restarts = c->opt.max_restarts;
+  d.restart_period = c->opt.restart_period;
+  d.stag_window = c->opt.stag_window;
+  d.rr_cutoff = c->opt.rr_cutoff > 0.0 ? c->opt.rr_cutoff : 1.4901161193847656e-08;   // sqrt(2^-52)
   d.lanes = lanes;
   return d;
 }
@@ -509,6 +522,8 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
   if (opt->block_threads != 0 && (opt->block_threads < 32 || opt->block_threads > kMaxThreads || opt->block_threads % 32))
     return set_error(PBCG_INVALID_ARG, "block_threads must be 0 or a multiple of 32 in [32, 1024]");
   if (opt->max_restarts < 0 || opt->max_restarts > 1000) return set_error(PBCG_INVALID_ARG, "max_restarts must be in [0, 1000]");
+  if (opt->restart_period < 0 || opt->stag_window < 0 || !(opt->rr_cutoff >= 0.0 && opt->rr_cutoff < 1.0))
+    return set_error(PBCG_INVALID_ARG, "restart_period and stag_window must be >= 0, rr_cutoff in [0, 1)");
   if (opt->cluster_blocks != 0 && opt->cluster_blocks != 1 && opt->cluster_blocks != 2 && opt->cluster_blocks != 4 &&
       opt->cluster_blocks != 8)
     return set_error(PBCG_INVALID_ARG, "cluster_blocks must be 0, 1, 2, 4 or 8");

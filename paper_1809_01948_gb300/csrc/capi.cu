@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <cstdint>
 #include <new>
 #include <string>
 
@@ -286,7 +287,8 @@ static void free_ctx(pbcg_ctx* c) {
   if (!c) return;
   if (c->valAu && c->valAu != (void*)c->val64) cudaFree(c->valAu);
   void* ptrs[] = {c->row_ptr, c->col, c->val64, c->valAt, c->diag64, c->dinv64, c->dinvT, c->st_mask,
-                  c->vecs, c->part, c->dstate, c->multi_vecs, c->multi_part, c->multi_state, c->multi_params};
+                  c->vecs, c->part, c->dstate, c->multi_vecs, c->multi_part, c->multi_state, c->multi_params,
+                  c->xbest};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->hstate) cudaFreeHost(c->hstate);
@@ -318,10 +320,16 @@ pbcg_status check_options(const pbcg_options* o, long long n) {
     return set_error(PBCG_INVALID_ARG, "options.operator_storage must be PBCG_STORAGE_AUTO or PBCG_STORAGE_GENERAL");
   if (o->method != PBCG_PIPELINED && o->method != PBCG_CLASSIC)
     return set_error(PBCG_INVALID_ARG, "options.method must be PBCG_PIPELINED or PBCG_CLASSIC");
+  if (o->restart_period < 0) return set_error(PBCG_INVALID_ARG, "options.restart_period must be >= 0");
+  if (o->stag_window < 0) return set_error(PBCG_INVALID_ARG, "options.stag_window must be >= 0");
+  if (!(o->rr_cutoff >= 0.0 && o->rr_cutoff < 1.0))
+    return set_error(PBCG_INVALID_ARG, "options.rr_cutoff must be in [0, 1)");
+  if (o->prefetch_trips > 16) return set_error(PBCG_INVALID_ARG, "options.prefetch_trips must be at most 16");
   if (o->method == PBCG_CLASSIC) {
     if (o->precision != PBCG_FP64) return set_error(PBCG_INVALID_ARG, "PBCG_CLASSIC runs in PBCG_FP64 only");
-    if (o->rr_period != 0 || o->rr_theta != 0.0 || o->rr_auto != 0 || o->max_restarts != 0)
-      return set_error(PBCG_INVALID_ARG, "PBCG_CLASSIC takes no replacement policy and no restarts");
+    if (o->rr_period != 0 || o->rr_theta != 0.0 || o->rr_auto != 0 || o->max_restarts != 0 ||
+        o->restart_period != 0 || o->stag_window != 0)
+      return set_error(PBCG_INVALID_ARG, "PBCG_CLASSIC takes no replacement or restart policy and no restarts");
   }
   (void)n;
   return PBCG_OK;
@@ -343,34 +351,43 @@ static bool streaming(const pbcg_ctx* c) {
          hot_bytes(c) > (double)l2_bytes();
 }
 
+// Four rows per thread in the hot passes (VEC kernels): stencil storage of a system whose
+// row count is a multiple of 4, Algorithm 2 without the automated policy, b, x and the
+// iterate history 16-byte aligned (the quads move as 128-bit accesses), and a block size
+// the kernels' 128-register budget allows (0 = their default, or at most 512 threads).
+bool quad_rows(const pbcg_ctx* c, const double* b, const double* x) {
+  const auto al = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
+  return c->stencil && c->n % 4 == 0 && !c->opt.rr_auto && c->opt.method == PBCG_PIPELINED && al(b) && al(x) &&
+         (c->opt.record_iterates == 0 || al(c->opt.hist_x)) &&
+         c->opt.block_threads <= pbcg::SolverLaunch<double, false, true>::kThreads;
+}
+
 template <typename T>
-static const void* kernel_ptr(const pbcg_ctx* c) {
+static const void* kernel_ptr(const pbcg_ctx* c, bool vec) {
   const pbcg_options& o = c->opt;
   const bool sc = scalar_jacobi(c);
   if constexpr (std::is_same<T, double>::value) {
-    if (o.method == PBCG_CLASSIC)
-      return sc ? (const void*)classic_kernel<double, true> : (const void*)classic_kernel<double, false>;
+    if (o.method == PBCG_CLASSIC) return classic_kernel_f64(sc);
+    return pipelined_kernel_f64(o.rr_auto != 0, sc, vec);
   } else {
-    if (streaming(c))
-      return sc ? (const void*)pbicgstab_kernel<float, false, true, true> : (const void*)pbicgstab_kernel<float, false, true>;
+    return pipelined_kernel_f32(o.rr_auto != 0, !vec && streaming(c), sc, vec);
   }
-  if (o.rr_auto) return (const void*)pbicgstab_kernel<T, true>;
-  return sc ? (const void*)pbicgstab_kernel<T, false, false, true> : (const void*)pbicgstab_kernel<T, false>;
 }
 
 // Default shape: the solver kernels' register budgets (SolverLaunch): one 1024-thread block
 // per SM (measured faster than two 512-thread blocks on the 2D and 3D convection-diffusion
 // systems: fewer blocks at each grid barrier and reduction), three 512-thread blocks per
-// SM for the streaming mixed build.
-static int kernel_threads(const pbcg_ctx* c) {
+// SM for the streaming mixed build, two 512-thread blocks for the four-row kernels.
+static int kernel_threads(const pbcg_ctx* c, bool vec) {
   if (c->opt.block_threads) return c->opt.block_threads;
+  if (vec) return pbcg::SolverLaunch<double, false, true>::kThreads;
   return streaming(c) ? pbcg::SolverLaunch<float, true>::kThreads : pbcg::SolverLaunch<double, false>::kThreads;
 }
 
-pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads) {
-  const int nt = kernel_threads(c);
+pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads, bool vec) {
+  const int nt = kernel_threads(c, vec);
   int per_sm = 0;
-  const void* k = c->precision == PBCG_MIXED ? kernel_ptr<float>(c) : kernel_ptr<double>(c);
+  const void* k = c->precision == PBCG_MIXED ? kernel_ptr<float>(c, vec) : kernel_ptr<double>(c, vec);
   cudaFuncAttributes fa;
   CK(cudaFuncGetAttributes(&fa, k), "kernel attributes");
   if (nt > fa.maxThreadsPerBlock)
@@ -598,6 +615,7 @@ extern "C" pbcg_status pbicgstab_create(pbcg_ctx** out, const pbcg_matrix* A, co
   if (st != PBCG_OK) { free_ctx(c); return st; }
   const size_t es = elem_size(c->precision);
   CKC(cudaMalloc(&c->vecs, es * (size_t)c->n * c->nvec), "cudaMalloc workspace");
+  CKC(cudaMalloc(&c->xbest, sizeof(double) * (size_t)c->n), "cudaMalloc best iterate");
   c->max_blocks = 4 * kMaxThreads;  // generous: any co-resident grid fits
   CKC(cudaMalloc(&c->part, sizeof(double) * 4 * kMaxDots * (size_t)c->max_blocks), "cudaMalloc partials");
   CKC(cudaStreamSynchronize(c->stream), "create");
@@ -637,20 +655,24 @@ pbcg_status enqueue_true_residual(pbcg_ctx* c, const double* b, const double* x,
 
 static pbcg_status enqueue_solve(pbcg_ctx* c, const double* b, double* x) {
   int grid = 0, threads = 0;
-  pbcg_status st = launch_shape(c, &grid, &threads);
+  const bool vec = quad_rows(c, b, x);
+  pbcg_status st = launch_shape(c, &grid, &threads, vec);
   if (st != PBCG_OK) return st;
-  st = check_barrier_budget(c->opt.max_it, c->opt.max_restarts, c->degree, grid);
+  st = check_barrier_budget(c->opt.max_it, c->opt.max_restarts, c->degree, grid, c->opt.restart_period,
+                            c->opt.stag_window);
   if (st != PBCG_OK) return st;
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->stream), "memset state");
   CK(cudaEventRecord(c->ev0, c->stream), "event record");
   if (c->precision == PBCG_MIXED) {
-    SolverParams<float> p = make_params<float>(c, b, x, grid);
+    SolverParams<float> p = make_params<float>(c, b, x, grid, vec);
+    c->launch[0] = grid; c->launch[1] = threads; c->launch[2] = vec ? 4 : 1; c->launch[3] = p.prefetch + 256 * p.overlap;
     void* args[] = {&p};
-    CK(cudaLaunchCooperativeKernel(kernel_ptr<float>(c), grid, threads, args, 0, c->stream), "cooperative launch");
+    CK(cudaLaunchCooperativeKernel(kernel_ptr<float>(c, vec), grid, threads, args, 0, c->stream), "cooperative launch");
   } else {
-    SolverParams<double> p = make_params<double>(c, b, x, grid);
+    SolverParams<double> p = make_params<double>(c, b, x, grid, vec);
+    c->launch[0] = grid; c->launch[1] = threads; c->launch[2] = vec ? 4 : 1; c->launch[3] = p.prefetch + 256 * p.overlap;
     void* args[] = {&p};
-    CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(c), grid, threads, args, 0, c->stream), "cooperative launch");
+    CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(c, vec), grid, threads, args, 0, c->stream), "cooperative launch");
   }
   CK(cudaEventRecord(c->ev1, c->stream), "event record");
   return enqueue_true_residual(c, b, x, &c->dstate->true_rel);
@@ -706,6 +728,35 @@ extern "C" pbcg_status pbicgstab_spmv(pbcg_ctx* c, const double* x, double* y) {
   const int nb = std::max(1, std::min(4 * sm_count(), (c->n + 255) / 256));
   spmv_kernel<<<nb, 256, 0, c->stream>>>(pbcg_view64(c), x, y);
   CK(cudaGetLastError(), "spmv kernel");
+  return PBCG_OK;
+}
+
+// dst_i = scale * src_i widened to FP64.
+template <typename T>
+__global__ void widen_kernel(int n, const T* src, double scale, double* dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = scale * (double)src[i];
+}
+
+extern "C" pbcg_status pbicgstab_get_vector(pbcg_ctx* c, int32_t which, double* dst) {
+  if (!c || !dst) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_get_vector");
+  // slot order of the workspace: r, rh, k, w, g, s, l, z (make_params)
+  if (which < PBCG_VEC_R || which > PBCG_VEC_Z) return set_error(PBCG_INVALID_ARG, "unknown vector %d", which);
+  // the scaled form keeps k, g, l multiplied by the constant diagonal d
+  const bool pre = which == PBCG_VEC_K || which == PBCG_VEC_G || which == PBCG_VEC_L;
+  const double scale = (pre && scalar_jacobi(c)) ? c->dconst_inv : 1.0;
+  const int nb = std::max(1, std::min(4 * sm_count(), (c->n + 255) / 256));
+  if (c->precision == PBCG_MIXED)
+    widen_kernel<float><<<nb, 256, 0, c->stream>>>(c->n, (const float*)c->vecs + (size_t)which * c->n, scale, dst);
+  else
+    widen_kernel<double><<<nb, 256, 0, c->stream>>>(c->n, (const double*)c->vecs + (size_t)which * c->n, scale, dst);
+  CK(cudaGetLastError(), "widen kernel");
+  return PBCG_OK;
+}
+
+extern "C" pbcg_status pbicgstab_launch_info(const pbcg_ctx* c, int32_t info[4]) {
+  if (!c || !info) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_launch_info");
+  for (int j = 0; j < 4; ++j) info[j] = c->launch[j];
   return PBCG_OK;
 }
 

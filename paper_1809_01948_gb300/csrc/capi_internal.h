@@ -10,6 +10,15 @@
 #include "solver.cuh"
 
 namespace pbcg {
+// Entry points of the persistent solver kernels (kernels_f64.cu, kernels_f32.cu,
+// kernels_vec.cu; compiled as separate translation units).  automated: Eq. (criterion)
+// policy; scalar: scaled-form Jacobi of a constant diagonal; stream: the 40-register mixed
+// build; vec: four rows per thread in the hot passes.
+const void* pipelined_kernel_f64(bool automated, bool scalar, bool vec);
+const void* pipelined_kernel_f32(bool automated, bool stream, bool scalar, bool vec);
+const void* classic_kernel_f64(bool scalar);
+const void* pipelined_kernel_f64_vec(bool scalar);
+const void* pipelined_kernel_f32_vec(bool scalar);
 pbcg_status set_error(pbcg_status st, const char* fmt, ...);
 pbcg_status cuda_status(cudaError_t e, const char* what);
 int sm_count();
@@ -82,6 +91,8 @@ struct pbcg_ctx {
   int max_blocks = 0;
   DevState* dstate = nullptr;
   DevState* hstate = nullptr;  // pinned
+  double* xbest = nullptr;     // best (re)start iterate of options.stag_window (n doubles)
+  int launch[4] = {0, 0, 0, 0};  // last solve: grid, threads, rows per thread, prefetch distance
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // multi-RHS workspace (grown on demand by pbicgstab_solve_multi)
   int multi_cap = 0;           // right-hand sides the buffers below hold
@@ -146,7 +157,8 @@ inline MatView<double> pbcg_view64(const pbcg_ctx* c) { return make_view<double>
 
 pbcg_status check_options(const pbcg_options* o, long long n);
 pbcg_status build_stencil(pbcg_ctx* c);
-pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads);
+pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads, bool vec);
+bool quad_rows(const pbcg_ctx* c, const double* b, const double* x);
 pbcg_status enqueue_true_residual(pbcg_ctx* c, const double* b, const double* x, double* out_dev);
 
 int l2_bytes();   // L2 size of the current device in bytes
@@ -161,14 +173,18 @@ inline bool scalar_jacobi(const pbcg_ctx* c) {
 // The grid barrier counts arrivals in 32 bits (barrier index x blocks).  An iteration
 // crosses at most 4d + 6 barriers (d = Neumann degree: two preconditioner applications,
 // passes A and B, a replacement and a failed stop test), a (re)start d + 2; keep the
-// solve's total times the blocks below 2^31 so the count cannot wrap.
-inline pbcg_status check_barrier_budget(int max_it, int max_restarts, int degree, int blocks) {
-  const long long per_it = 8 + 4LL * degree;
-  const long long starts = (4 + 2LL * degree) * ((long long)max_restarts + 1);
+// solve's total times the blocks below 2^31 so the count cannot wrap.  With a restart
+// policy every iteration may end in a restart (a failed stop-test verification restarts).
+inline pbcg_status check_barrier_budget(int max_it, int max_restarts, int degree, int blocks,
+                                        int restart_period = 0, int stag_window = 0) {
+  const long long start = 4 + 2LL * degree;
+  const long long per_it = 8 + 4LL * degree + (restart_period > 0 ? start : 0);
+  const long long fixed = start * ((long long)max_restarts + 1 + (restart_period > 0 ? 1 : 0)) +
+                          (stag_window > 0 ? 2 : 0);
   const long long budget = ((1LL << 31) - 1) / blocks;       // barriers the counter allows
-  if (((long long)max_it + 1) * per_it + starts > budget)
+  if (((long long)max_it + 1) * per_it + fixed > budget)
     return pbcg::set_error(PBCG_INVALID_ARG, "max_it %d is too large for %d blocks per barrier (at most %lld)",
-                           max_it, blocks, (budget - starts) / per_it - 1);
+                           max_it, blocks, (budget - fixed) / per_it - 1);
   return PBCG_OK;
 }
 
@@ -181,13 +197,15 @@ inline double hot_bytes(const pbcg_ctx* c) {
   return (double)c->n * (12.0 * es + 16.0 + op);
 }
 
+// vec: the four-row kernels, whose per-block chunks start at multiples of 4.
 template <typename T>
-inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int grid) {
+inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int grid, bool vec = false) {
   SolverParams<T> p;
   memset(&p, 0, sizeof p);
   const int n = c->n;
   p.n = n;
   p.chunk = (n + grid - 1) / grid;
+  if (vec) p.chunk = (p.chunk + 3) / 4 * 4;
   const T* at = c->valAt ? (const T*)c->valAt : (const T*)c->valAu;
   p.At = make_view<T>(c, at, c->valAt != nullptr);
   if (!c->valAt && c->fmt == PBCG_FMT_DIA) p.At = make_view<T>(c, at, false);
@@ -219,10 +237,20 @@ inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int 
   const double tms = c->opt.timeout_ms > 0 ? c->opt.timeout_ms : 2000.0;
   p.timeout_ns = (unsigned long long)(tms * 1e6);
   p.max_restarts = c->opt.max_restarts;
+  p.restart_period = c->opt.restart_period;
+  p.stag_window = c->opt.stag_window;
+  p.xbest = c->xbest;
+  p.rr_cutoff = c->opt.rr_cutoff > 0.0 ? c->opt.rr_cutoff : 1.4901161193847656e-08;   // sqrt(2^-52)
   p.strided = c->bandwidth > p.chunk / 2 ? 1 : 0;
+  p.halo = c->bandwidth;
+  p.overlap = (c->opt.barrier_overlap > 0 && !p.strided && c->prec_kind != PBCG_PREC_NEUMANN &&
+               c->opt.method == PBCG_PIPELINED && !c->opt.rr_auto && grid > 1 && p.chunk > 2 * c->bandwidth) ? 1 : 0;
   // stencil storage only: with CSR / DIA values the row products already keep several
   // loads per row in flight (measured slower with the prefetch on the 3D CSR operator)
-  p.prefetch = (c->stencil && hot_bytes(c) > (double)l2_bytes()) ? 1 : 0;
+  // automatic: the one-row kernels of a stencil system whose working set exceeds L2 (the
+  // four-row kernels keep enough loads in flight without it: measured no faster with it)
+  p.prefetch = (c->stencil && !vec && hot_bytes(c) > (double)l2_bytes()) ? 1 : 0;
+  if (c->opt.prefetch_trips != 0) p.prefetch = c->opt.prefetch_trips > 0 ? c->opt.prefetch_trips : 0;
   p.rr_tau = c->opt.rr_tau > 0.0 ? c->opt.rr_tau : 1.4901161193847656e-08;
   p.bnd_msn = (double)c->maxnnz * sqrt((double)n);
   p.bnd_tmsn = sqrt((double)n);

@@ -111,6 +111,78 @@ __device__ __forceinline__ Acc row_dot_fn(const MatView<V>& A, int i, F xj) {
   return acc;
 }
 
+// ---------------------------------------------------------------- four rows per thread
+// The structured-stencil operator is applied to four consecutive rows i0 .. i0+3 at a
+// time (i0 a multiple of 4, n a multiple of 4, 16-byte aligned vectors): own-row vectors
+// move as one 128-bit access (two for FP64), and each stencil offset reads the one or two
+// aligned quads that hold its four neighbours.  Those loads depend only on the row index
+// (a quad is read whenever it lies inside 0 .. n-1), so they are issued together with the
+// mask load instead of after it; the mask then decides which products enter each row.
+template <typename T> struct Quad { T v[4]; };
+
+template <typename T> __device__ __forceinline__ Quad<T> ld4(const T* p, int i);
+template <> __device__ __forceinline__ Quad<float> ld4<float>(const float* p, int i) {
+  const float4 f = *reinterpret_cast<const float4*>(p + i);
+  return Quad<float>{{f.x, f.y, f.z, f.w}};
+}
+template <> __device__ __forceinline__ Quad<double> ld4<double>(const double* p, int i) {
+  const double2 a = *reinterpret_cast<const double2*>(p + i);
+  const double2 b = *reinterpret_cast<const double2*>(p + i + 2);
+  return Quad<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* p, int i, const Quad<float>& q) {
+  *reinterpret_cast<float4*>(p + i) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+}
+__device__ __forceinline__ void st4(double* p, int i, const Quad<double>& q) {
+  *reinterpret_cast<double2*>(p + i) = make_double2(q.v[0], q.v[1]);
+  *reinterpret_cast<double2*>(p + i + 2) = make_double2(q.v[2], q.v[3]);
+}
+
+// The presence masks of rows i0 .. i0+3 (one 8-byte load).
+__device__ __forceinline__ void ld_mask4(const unsigned short* __restrict__ mask, int i0, unsigned (&m)[4]) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(mask + i0));
+  m[0] = u.x & 0xffffu; m[1] = u.x >> 16; m[2] = u.y & 0xffffu; m[3] = u.y >> 16;
+}
+
+// y_{i0+j} = sum_d c_d x_{i0+j+off_d} over the offsets present in row i0+j (stencil view),
+// products summed in ascending offset order as row_dot does: the same value per row.
+template <typename Acc, typename V, typename X>
+__device__ __forceinline__ Quad<Acc> quad_dot(const MatView<V>& A, const X* __restrict__ x, int i0,
+                                              const unsigned (&m)[4]) {
+  Quad<Acc> acc;
+  if (A.unit_diag) {
+    const Quad<X> c = ld4(x, i0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc.v[j] = Acc(c.v[j]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc.v[j] = Acc(0);
+  }
+  const int n = A.n;
+#pragma unroll 2
+  for (int d = 0; d < A.ndiag; ++d) {
+    const int off = A.off[d];
+    const unsigned bit = A.mbit[d];
+    const Acc c = Acc(A.cval[d]);
+    const int r = off & 3;             // neighbour quad misalignment (two's complement)
+    const int a = i0 + off - r;        // first of the aligned quads holding the neighbours
+    Quad<X> lo, hi;
+    lo.v[0] = lo.v[1] = lo.v[2] = lo.v[3] = X(0);
+    hi = lo;
+    if (a >= 0 && a < n) lo = ld4(x, a);
+    if (r != 0 && a + 4 >= 0 && a + 4 < n) hi = ld4(x, a + 4);
+    X e[4];
+    if (r == 0) { e[0] = lo.v[0]; e[1] = lo.v[1]; e[2] = lo.v[2]; e[3] = lo.v[3]; }
+    else if (r == 1) { e[0] = lo.v[1]; e[1] = lo.v[2]; e[2] = lo.v[3]; e[3] = hi.v[0]; }
+    else if (r == 2) { e[0] = lo.v[2]; e[1] = lo.v[3]; e[2] = hi.v[0]; e[3] = hi.v[1]; }
+    else { e[0] = lo.v[3]; e[1] = hi.v[0]; e[2] = hi.v[1]; e[3] = hi.v[2]; }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((m[j] >> bit) & 1u) acc.v[j] = fma(c, Acc(e[j]), acc.v[j]);
+  }
+  return acc;
+}
+
 // Hint: bring the 128-byte line holding *ptr into L2 (no register is written, so a
 // thread can request the next row's operands while it computes the current one).
 template <typename V>
@@ -163,6 +235,39 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned epoch, 
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// The same barrier in two halves, so that a block can do work that needs no other block's
+// writes between its arrival and its wait (the single-GPU form of hiding a global
+// reduction behind computation).  grid_arrive publishes this block's earlier writes
+// (block-wide __syncthreads, then one release by thread 0); grid_wait returns once all
+// nblk blocks arrived at barrier `epoch` (false: timeout here or elsewhere).
+__device__ __forceinline__ void grid_arrive(unsigned* counter) {
+  __syncthreads();
+  if (threadIdx.x == 0) red_release_add(counter, 1u);
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned* counter, unsigned epoch, unsigned nblk, int* err,
+                                          unsigned long long timeout_ns) {
+  __shared__ int s_ok2;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = epoch * nblk;
+    const unsigned long long t0 = global_ns();
+    unsigned spins = 0;
+    while (ld_acquire_u32(counter) < target) {
+      if ((++spins & 63u) == 0 && (global_ns() - t0 > timeout_ns || *(volatile int*)err)) {
+        atomicCAS(err, 0, (int)kTimeout);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    if (ok && *(volatile int*)err) ok = 0;
+    s_ok2 = ok;
+  }
+  __syncthreads();
+  return s_ok2 != 0;
 }
 
 // ---------------------------------------------------------------- reductions

@@ -133,6 +133,8 @@ static pbcg_status launch_wave(pbcg_ctx* c, int teams, int bpt, int nt, const do
     p.K = 0;
     p.hist_s = nullptr;
     p.hist_len = 0;
+    p.xbest = nullptr;   // stagnation is detected per column, but the last iterate is returned
+    p.overlap = 0;       // the teams run plain barriers
     hp[t] = p;
   }
   MCK(cudaMemcpyAsync(c->multi_params, hp, sizeof(SolverParams<T>) * teams, cudaMemcpyHostToDevice, c->stream),
@@ -160,7 +162,8 @@ extern "C" pbcg_status pbicgstab_solve_multi(pbcg_ctx* c, int32_t nrhs, const do
   // blocks per team: share the grid, at least 32 rows per block
   int bpt = std::max(1, G / teams);
   bpt = (int)std::min<long long>(bpt, std::max<long long>(1, (c->n + 31) / 32));
-  pbcg_status st = check_barrier_budget(c->opt.max_it, c->opt.max_restarts, c->degree, bpt);
+  pbcg_status st = check_barrier_budget(c->opt.max_it, c->opt.max_restarts, c->degree, bpt, c->opt.restart_period,
+                                        c->opt.stag_window);
   if (st != PBCG_OK) return st;
   st = ensure_multi(c, teams, bpt);
   if (st != PBCG_OK) return st;

@@ -3,7 +3,6 @@
 // array of fixed size; nothing here calls cudaMalloc/cudaFree or an allocating
 // library routine.
 #include <cstring>
-#include <mutex>
 
 #include "../../include/pbicgstab.h"
 #include "capi_internal.h"
@@ -63,26 +62,15 @@ __global__ void na_diag_range(int n, const double* diag, unsigned long long* ran
   }
 }
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_scratch for the current device.  In host code the name
-// g_scratch is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// Device address of g_scratch in the current context.  In host code the name g_scratch
+// is only a host-side stand-in, so the address comes from cudaGetSymbolAddress, with the
+// device current.  It is looked up on every call (the lookup allocates nothing): a cached
+// address could be stale after cudaDeviceReset or in another context of the same device.
 pbcg_status scratch_address(void** out) {
-  int dev = 0;
-  pbcg_status st = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+  void* p = nullptr;
+  pbcg_status st = cuda_status(cudaGetSymbolAddress(&p, g_scratch), "cudaGetSymbolAddress(scratch)");
   if (st != PBCG_OK) return st;
-  if (dev < 0 || dev >= kMaxDevices) return set_error(PBCG_INVALID_ARG, "device ordinal %d not supported", dev);
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    st = cuda_status(cudaGetSymbolAddress(&p, g_scratch), "cudaGetSymbolAddress(scratch)");
-    if (st != PBCG_OK) return st;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return PBCG_OK;
 }
 
@@ -176,11 +164,11 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   if (opt->precision != PBCG_FP64) return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_noalloc supports FP64 only");
   if (M->kind != PBCG_PREC_NONE && M->kind != PBCG_PREC_JACOBI)
     return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_noalloc supports no preconditioner or Jacobi");
-  if (opt->max_it < 0 || !(opt->tol >= 0.0) || opt->rr_period < 0 || opt->rr_auto != 0 ||
-      !(opt->rr_theta >= 0.0 && opt->rr_theta < 1.0) || opt->record_iterates < 0 ||
-      opt->max_restarts < 0 || opt->max_restarts > 1000 || opt->rr_auto != 0 ||
-      (opt->record_iterates > 0 && !opt->hist_x) || opt->hist_len < 0 || (opt->hist_len > 0 && !opt->hist_scalars))
-    return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_noalloc: invalid options");
+  {
+    const pbcg_status os = check_options(opt, A->n);   // the context solver's option checks
+    if (os != PBCG_OK) return os;
+  }
+  if (opt->rr_auto != 0) return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_noalloc does not run the automated policy");
   if (opt->method != PBCG_PIPELINED) return set_error(PBCG_INVALID_ARG, "pbicgstab_solve_noalloc runs Algorithm 2 only");
   const int n = (int)A->n;
   MatView<double> A64;
@@ -259,21 +247,25 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
       dconst_inv = 1.0 / d;
     }
   }
-  // launch shape: the same rule as the context-based solver
-  const int nt = opt->block_threads ? opt->block_threads : 512;
-  if (nt < 32 || nt > kMaxThreads || nt % 32) return set_error(PBCG_INVALID_ARG, "bad block_threads");
-  // Jacobi with a constant diagonal runs the scaled-form build
-  const void* kern = (jac && dconst) ? (const void*)pbicgstab_kernel<double, false, false, true>
-                                     : (const void*)pbicgstab_kernel<double, false>;
+  // launch shape: the context-based solver's default rule (one 1024-thread block per SM,
+  // every co-resident block slot busy but at least 32 rows per block), so that a call with
+  // default options sums its dot products in the same order as pbicgstab_solve
+  const void* kern = pipelined_kernel_f64(false, jac && dconst, false);
+  const int nt = opt->block_threads ? opt->block_threads : pbcg::SolverLaunch<double, false>::kThreads;
+  cudaFuncAttributes fa;
+  NCK(cudaFuncGetAttributes(&fa, kern), "kernel attributes");
+  if (nt > fa.maxThreadsPerBlock)
+    return set_error(PBCG_INVALID_ARG, "block_threads %d above this solver's limit of %d", nt, fa.maxThreadsPerBlock);
   int per_sm = 0;
   NCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, 0), "occupancy");
-  const int sms = sm_count();
-  const int max_co = std::min(per_sm * sms, kMaxGrid);
+  if (per_sm <= 0) return set_error(PBCG_INVALID_ARG, "kernel cannot be resident with %d threads per block", nt);
+  const int max_co = std::min(per_sm * sm_count(), kMaxGrid);
   int grid = opt->grid_blocks;
-  if (grid == 0) grid = (int)std::min<long long>(std::max<long long>(1, (n + 31) / 32), std::min(max_co, 2 * sms));
+  if (grid == 0) grid = (int)std::min<long long>(std::max<long long>(1, (n + 31) / 32), (long long)max_co);
   if (grid < 1 || grid > max_co) return set_error(PBCG_INVALID_ARG, "grid_blocks %d above %d", grid, max_co);
   {
-    const pbcg_status bs = check_barrier_budget(opt->max_it, opt->max_restarts, 0, grid);
+    const pbcg_status bs = check_barrier_budget(opt->max_it, opt->max_restarts, 0, grid, opt->restart_period,
+                                                opt->stag_window);
     if (bs != PBCG_OK) return bs;
   }
   SolverParams<double> p;
@@ -317,6 +309,10 @@ extern "C" pbcg_status pbicgstab_solve_noalloc(const pbcg_matrix* A, const pbcg_
   const double tms = opt->timeout_ms > 0 ? opt->timeout_ms : 2000.0;
   p.timeout_ns = (unsigned long long)(tms * 1e6);
   p.max_restarts = opt->max_restarts;
+  p.restart_period = opt->restart_period;
+  p.stag_window = opt->stag_window;
+  p.xbest = p.tmpa;   // FP64 and no Neumann sweeps here: the sweep temporary is free
+  p.rr_cutoff = opt->rr_cutoff > 0.0 ? opt->rr_cutoff : 1.4901161193847656e-08;   // sqrt(2^-52)
   // row order: the same rule as the context-based solver
   int bandwidth = 0;
   if (A64.fmt == 0) bandwidth = h.reserved;

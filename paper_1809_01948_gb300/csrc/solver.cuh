@@ -23,6 +23,7 @@
 // same order, so all blocks take identical control-flow decisions without any
 // extra synchronisation.
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 
 namespace pbcg {
@@ -68,7 +69,15 @@ struct SolverParams {
   unsigned long long timeout_ns;
   int max_restarts;     // restarts from the current iterate allowed after a breakdown
   int strided;          // grid team row order: 1 grid-stride, 0 one contiguous chunk per block
-  int prefetch;         // 1: request the next row's operands into L2 (working set above L2)
+  int prefetch;         // > 0: request the operands of the row sweep this many trips ahead into L2
+  int overlap;          // 1: compute the next SpMV on a block's interior rows inside each grid
+                        // barrier (chunked row order, no Neumann); 0: plain barriers
+  int halo;             // max |col - row| of A: rows farther than this from a block's chunk
+                        // ends have all their SpMV operands in the block's own rows
+  int restart_period;   // > 0: restart from the current iterate every P iterations (reading R20)
+  int stag_window;      // > 0: progress-based stagnation (reading R21)
+  double* xbest;        // FP64 n-vector for R21's best iterate, or nullptr (no fallback)
+  double rr_cutoff;     // periodic replacements stop once ||r_i|| < rr_cutoff ||r_0||
   // automated replacement, Eq. (criterion) with the gap bound f^r of Eq. (DDr_bound)
   // (read only by kernels instantiated with AUTO = true)
   double rr_tau;
@@ -184,6 +193,8 @@ struct GridTeam {
   // consecutive rows together, so neighbours farther away than a chunk (the +-plane
   // couplings of a 3D stencil) are read from L2 while the window still holds them.
   int first, stride, end;
+  int first4, stride4;   // four-row (VEC) passes: first row of this thread's first quad is
+                         // first4 + 4 * threadIdx.x, then every stride4 rows, below end
   int bid;        // this block's index within the team
   int nblk;       // blocks in the team (the whole grid, or one sub-grid of a multi solve)
   unsigned epoch;
@@ -194,6 +205,8 @@ struct GridTeam {
   double* smem;   // >= kWork + kMaxDots doubles
   double* scal;   // >= 8 doubles of shared memory for scalar broadcasts
   __device__ __forceinline__ bool sync() { return grid_barrier(bar, ++epoch, (unsigned)nblk, err, timeout_ns); }
+  __device__ __forceinline__ void arrive() { grid_arrive(bar); ++epoch; }
+  __device__ __forceinline__ bool wait() { return grid_wait(bar, epoch, (unsigned)nblk, err, timeout_ns); }
   template <int ND>
   __device__ __forceinline__ void publish(double (&v)[ND], int set) {
     block_publish<ND>(v, smem, part + (size_t)set * nblk * kMaxDots, bid);
@@ -289,7 +302,7 @@ __device__ __forceinline__ T minv_local(const SolverParams<T, VR>& p, T v, int i
 // Jacobi sweeps y_1 = D^{-1}src + D^{-1}(src - (A D^{-1}) src),
 // y_j = y_{j-1} + D^{-1}(src - A y_{j-1}); one or two vectors at once.
 // Returns false if the grid must stop.
-template <typename T, typename VR, typename Team>
+template <bool VEC = false, typename T, typename VR, typename Team>
 __device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T* src0, T* dst0, const T* src1,
                               T* dst1) {
   const int row0 = team.first, rstride = team.stride, row1 = team.end;
@@ -299,9 +312,57 @@ __device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T*
   for (int j = 1; j <= d; ++j) {
     T* out0 = ((d - j) % 2 == 0) ? dst0 : p.tmpa;
     T* out1 = ((d - j) % 2 == 0) ? dst1 : p.tmpb;
+    if constexpr (VEC) {
+      // four rows per thread; the stencil storage has one diagonal value (dinv_c)
+      const T di = p.dinv_c;
+      for (int i0 = team.first4 + 4 * threadIdx.x; i0 < row1; i0 += team.stride4) {
+        if (p.prefetch && (threadIdx.x & 3) == 0 && i0 + p.prefetch * team.stride4 < row1) {
+          const int jn = i0 + p.prefetch * team.stride4;
+          prefetch_l2(src0 + jn);
+          if (j > 1) prefetch_l2(prev0 + jn);
+          if (src1) { prefetch_l2(src1 + jn); if (j > 1) prefetch_l2(prev1 + jn); }
+        }
+        unsigned mk[4];
+        ld_mask4(p.Au.mask, i0, mk);
+        {
+          const Quad<T> sv = ld4(src0, i0);
+          Quad<T> o;
+          if (j == 1) {
+            const Quad<T> as = quad_dot<T>(p.At, src0, i0, mk);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o.v[q] = fma(di, sv.v[q] - as.v[q], di * sv.v[q]);
+          } else {
+            const Quad<T> ap = quad_dot<T>(p.Au, prev0, i0, mk);
+            const Quad<T> pv = ld4(prev0, i0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o.v[q] = fma(di, sv.v[q] - ap.v[q], pv.v[q]);
+          }
+          st4(out0, i0, o);
+        }
+        if (src1) {
+          const Quad<T> sv = ld4(src1, i0);
+          Quad<T> o;
+          if (j == 1) {
+            const Quad<T> as = quad_dot<T>(p.At, src1, i0, mk);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o.v[q] = fma(di, sv.v[q] - as.v[q], di * sv.v[q]);
+          } else {
+            const Quad<T> ap = quad_dot<T>(p.Au, prev1, i0, mk);
+            const Quad<T> pv = ld4(prev1, i0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o.v[q] = fma(di, sv.v[q] - ap.v[q], pv.v[q]);
+          }
+          st4(out1, i0, o);
+        }
+      }
+      if (!team.sync()) return false;
+      prev0 = out0;
+      prev1 = out1;
+      continue;
+    }
     for (int i = row0 + threadIdx.x; i < row1; i += rstride) {
-      if (p.prefetch && i + rstride < row1) {
-        const int jn = i + rstride;
+      if (p.prefetch && i + p.prefetch * rstride < row1) {
+        const int jn = i + p.prefetch * rstride;
         prefetch_l2(src0 + jn);
         if (j > 1) prefetch_l2(prev0 + jn);
         if (src1) { prefetch_l2(src1 + jn); if (j > 1) prefetch_l2(prev1 + jn); }
@@ -418,9 +479,157 @@ __device__ void spmv_lanes(const Team& team, const MatView<T>& A, const T* x, T*
   __syncthreads();
 }
 
+// Interior of a block's chunk (chunked row order): rows [lo, hi) whose SpMV operands, rows
+// within +-halo, all belong to the block.  Their products need no other block's writes, so
+// the block computes them between arriving at a grid barrier and waiting on it.  The quad
+// passes use the quads inside [lo, hi): first row a multiple of 4 from lo4 = lo rounded up.
+struct Interior {
+  int lo, hi, lo4;
+  __device__ __forceinline__ bool row(int i) const { return i >= lo && i < hi; }
+  __device__ __forceinline__ bool quad(int i0) const { return i0 >= lo4 && i0 + 3 < hi; }
+};
+
+template <typename T, typename VR, typename Team>
+__device__ __forceinline__ Interior interior_of(const SolverParams<T, VR>& p, const Team& team) {
+  Interior in;
+  in.lo = team.first + p.halo;
+  in.hi = team.end - p.halo;
+  in.lo4 = (in.lo + 3) & ~3;
+  if (!p.overlap || in.hi <= in.lo) in.lo = in.hi = in.lo4 = 0;   // empty
+  return in;
+}
+
+// y = At x on the interior rows (the row mapping need not match the passes': the grid_wait
+// after it synchronises the block).
+template <bool VEC, typename T, typename VR, typename Team>
+__device__ __forceinline__ void interior_product(const SolverParams<T, VR>& p, const Team& team, const Interior& in,
+                                                 const T* x, T* y) {
+  if constexpr (VEC) {
+    for (int i0 = in.lo4 + 4 * threadIdx.x; i0 + 3 < in.hi; i0 += 4 * blockDim.x) {
+      unsigned mk[4];
+      ld_mask4(p.At.mask, i0, mk);
+      st4(y, i0, quad_dot<T>(p.At, x, i0, mk));
+    }
+  } else {
+    for (int i = in.lo + threadIdx.x; i < in.hi; i += blockDim.x) y[i] = row_dot<T>(p.At, x, i);
+  }
+}
+
+// Pass A on four rows per thread (stencil storage, VEC kernels): the same per-row
+// arithmetic as the one-row loop in solve_body, rows taken a quad at a time.
+template <bool SCALAR, typename T, typename VR, typename Team, typename Acc>
+__device__ __forceinline__ void pass_a_quads(const SolverParams<T, VR>& p, const Team& team, T aT, T bT, T opT,
+                                             bool rep_last, const Interior& pre, Acc& a_qy, Acc& a_yy) {
+  const bool neu = p.prec == 2;
+  const int row1 = team.end;
+  for (int i0 = team.first4 + 4 * threadIdx.x; i0 < row1; i0 += team.stride4) {
+    if (p.prefetch && (threadIdx.x & 3) == 0 && i0 + p.prefetch * team.stride4 < row1) {   // later quads, into L2
+      const int j = i0 + p.prefetch * team.stride4;
+      prefetch_l2(p.w + j); prefetch_l2(p.z + j); prefetch_l2(p.k + j); prefetch_l2(p.g + j);
+      prefetch_l2(p.l + j); prefetch_l2(p.s + j); prefetch_l2(p.v + j); prefetch_l2(p.r + j);
+      if (neu) { prefetch_l2(p.m + j); prefetch_l2(p.nn + j); }
+    }
+    unsigned mk[4];
+    ld_mask4(p.Au.mask, i0, mk);
+    const Quad<T> W = ld4(p.w, i0), Z = ld4(p.z, i0), K = ld4(p.k, i0), G = ld4(p.g, i0);
+    const Quad<T> L = ld4(p.l, i0), S = ld4(p.s, i0), V = ld4(p.v, i0), R = ld4(p.r, i0);
+    Quad<T> M, NP;
+    if (neu) {
+      M = ld4(p.m, i0);
+      NP = ld4(p.nn, i0);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) M.v[q] = minv_local<SCALAR>(p, W.v[q], i0 + q);
+      if (rep_last) NP = ld4(p.nb, i0);
+      else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) NP.v[q] = minv_local<SCALAR>(p, Z.v[q], i0 + q);
+      }
+    }
+    const Quad<T> Tq = pre.quad(i0) ? ld4(p.t, i0)                      // t_i = A m_i (inside the last barrier)
+                       : neu ? quad_dot<T>(p.Au, p.m, i0, mk) : quad_dot<T>(p.At, p.w, i0, mk);
+    Quad<T> Gn, Sn, Ln, Zn;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Gn.v[q] = fma(bT, fma(-opT, L.v[q], G.v[q]), K.v[q]);    // g_i
+      Sn.v[q] = fma(bT, fma(-opT, Z.v[q], S.v[q]), W.v[q]);    // s_i
+      Ln.v[q] = fma(bT, fma(-opT, NP.v[q], L.v[q]), M.v[q]);   // l_i
+      Zn.v[q] = fma(bT, fma(-opT, V.v[q], Z.v[q]), Tq.v[q]);   // z_i
+      const T qq = fma(-aT, Sn.v[q], R.v[q]);                  // q_i
+      const T y = fma(-aT, Zn.v[q], W.v[q]);                   // y_i
+      a_qy.add(qq, y);
+      a_yy.add(y, y);
+    }
+    st4(p.g, i0, Gn); st4(p.s, i0, Sn); st4(p.l, i0, Ln); st4(p.z, i0, Zn); st4(p.t, i0, Tq);
+  }
+}
+
+// Pass B on four rows per thread (see pass_a_quads).
+template <bool SCALAR, typename T, typename VR, typename Team, typename Acc>
+__device__ __forceinline__ void pass_b_quads(const SolverParams<T, VR>& p, const Team& team, T aT, T oT, double ax,
+                                             double ox, bool hist, int it, bool do_rr, const Interior& pre,
+                                             Acc& a_rr, Acc& a_rw, Acc& a_rs, Acc& a_rz, Acc& a_r2) {
+  const bool neu = p.prec == 2;
+  const int row1 = team.end;
+  const size_t n = (size_t)p.n;
+  for (int i0 = team.first4 + 4 * threadIdx.x; i0 < row1; i0 += team.stride4) {
+    if (p.prefetch && (threadIdx.x & 3) == 0 && i0 + p.prefetch * team.stride4 < row1) {
+      const int j = i0 + p.prefetch * team.stride4;
+      prefetch_l2(p.z + j); prefetch_l2(p.w + j); prefetch_l2(p.r + j); prefetch_l2(p.s + j);
+      prefetch_l2(p.k + j); prefetch_l2(p.l + j); prefetch_l2(p.g + j); prefetch_l2(p.t + j);
+      prefetch_l2(p.x + j); prefetch_l2(p.rh + j);
+      if (neu) { prefetch_l2(p.m + j); prefetch_l2(p.nn + j); }
+    }
+    unsigned mk[4];
+    ld_mask4(p.Au.mask, i0, mk);
+    const Quad<T> Z = ld4(p.z, i0), W = ld4(p.w, i0), R = ld4(p.r, i0), S = ld4(p.s, i0);
+    const Quad<T> K = ld4(p.k, i0), L = ld4(p.l, i0), G = ld4(p.g, i0), Tt = ld4(p.t, i0);
+    const Quad<double> X = ld4(p.x, i0);
+    Quad<T> N, M;
+    if (neu) {
+      N = ld4(p.nn, i0);
+      M = ld4(p.m, i0);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        N.v[q] = minv_local<SCALAR>(p, Z.v[q], i0 + q);
+        M.v[q] = minv_local<SCALAR>(p, W.v[q], i0 + q);
+      }
+    }
+    const Quad<T> Vq = pre.quad(i0) ? ld4(p.v, i0)                      // v_i = A n_i (inside the last barrier)
+                       : neu ? quad_dot<T>(p.Au, p.nn, i0, mk) : quad_dot<T>(p.At, p.z, i0, mk);
+    Quad<double> Xn;
+    Quad<T> Rn, Kn, Wn;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T qq = fma(-aT, S.v[q], R.v[q]);
+      const T u = fma(-aT, L.v[q], K.v[q]);
+      const T y = fma(-aT, Z.v[q], W.v[q]);
+      Xn.v[q] = fma(ox, (double)u, fma(ax, (double)G.v[q], X.v[q]));   // x_{i+1}
+      Rn.v[q] = fma(-oT, y, qq);                                          // r_{i+1}
+      Kn.v[q] = fma(-oT, fma(-aT, N.v[q], M.v[q]), u);                   // k_{i+1}
+      Wn.v[q] = fma(-oT, fma(-aT, Vq.v[q], Tt.v[q]), y);                 // w_{i+1}
+    }
+    st4(p.x, i0, Xn); st4(p.v, i0, Vq); st4(p.r, i0, Rn); st4(p.k, i0, Kn); st4(p.w, i0, Wn);
+    if (hist) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) p.hist_x[(size_t)it * n + i0 + q] = Xn.v[q];
+    }
+    if (!do_rr) {
+      const Quad<T> RH = ld4(p.rh, i0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a_rr.add(RH.v[q], Rn.v[q]); a_rw.add(RH.v[q], Wn.v[q]); a_rs.add(RH.v[q], S.v[q]);
+        a_rz.add(RH.v[q], Z.v[q]); a_r2.add(Rn.v[q], Rn.v[q]);
+      }
+    }
+  }
+}
+
 // The whole solve (Algorithm 2 + Eq. rr) for one system, executed by a team.
-template <bool AUTO, bool SCALAR, typename T, typename VR, typename Team>
+template <bool AUTO, bool SCALAR, bool VEC = false, typename T, typename VR, typename Team>
 __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
+  static_assert(!(VEC && AUTO), "the four-row passes run without the automated policy");
   using Acc = typename AccOf<T>::type;
   const int n = p.n;
   // automated replacement state, used by thread 0 only (AUTO kernels)
@@ -430,10 +639,14 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   const bool neu = p.prec == 2;
   const bool leader = team.leader();
   int nrep = 0;
-  int nrestart = 0;
+  int nrestart = 0;           // restarts after breakdowns (bounded by max_restarts)
+  int nperiodic = 0;          // periodic restarts (reading R20)
   int it = 0;                 // completed iterations, across restarts
   bool first = true;
   double rn0 = 0.0;
+  // reading R21: reference true residual, the iteration it was set, best true residual
+  double ref_true = INFINITY, best_true = INFINITY;
+  int ref_it = 0;
 
 #define PBCG_SYNC() \
   do { if (!team.sync()) return; } while (0)
@@ -450,7 +663,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   do {                                                                                   \
     if (leader) {                                                                        \
       p.res->status = (st); p.res->iterations = (its); p.res->nrep = nrep;               \
-      p.res->nrestart = nrestart; p.res->rn_rel = (rnv) / bn;                            \
+      p.res->nrestart = nrestart + nperiodic; p.res->rn_rel = (rnv) / bn;                \
     }                                                                                    \
     return;                                                                              \
   } while (0)
@@ -462,7 +675,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   // ---------------- initialisation of Algorithm 2
   {
     Acc a_rr;
-    DAcc a_bb, a_xx;
+    DAcc a_bb, a_xx, a_tr;
     PBCG_ROWS {
       const double bi = p.b[i];
       if (AUTO) { const double xi = p.x[i]; a_xx.add(xi, xi); }
@@ -475,10 +688,12 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       if (neu) p.nn[i] = T(0);
       a_rr.add(ri, ri);
       a_bb.add(bi, bi);
+      if constexpr (!std::is_same<T, double>::value) a_tr.add(r64, r64);   // FP64 ||b - A x||^2
     }
-    double v3[3] = {a_rr.value(), a_bb.value(), a_xx.value()};
-    if (AUTO) team.template publish<3>(v3, 0);
-    else team.template publish<2>(*reinterpret_cast<double(*)[2]>(v3), 0);
+    double v4[4] = {a_rr.value(), a_bb.value(), std::is_same<T, double>::value ? a_rr.value() : a_tr.value(),
+                    a_xx.value()};
+    if (AUTO) team.template publish<4>(v4, 0);
+    else team.template publish<3>(*reinterpret_cast<double(*)[3]>(v4), 0);
   }
   PBCG_SYNC();
   if (neu && !neumann_apply(p, team, p.r, p.k, (const T*)nullptr, (T*)nullptr)) return;
@@ -493,26 +708,28 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     team.template publish<1>(v1, 1);
   }
   PBCG_SYNC();
-  double rho, rw0, bn, rn, alpha, tolb;
+  double rho, rw0, bn, rn, alpha, tolb, rtrue;
   {
-    double t3[3] = {0.0, 0.0, 0.0};
-    if (AUTO) team.template combine<3>(0, t3);
-    else team.template combine<2>(0, *reinterpret_cast<double(*)[2]>(t3));
+    double t4[4] = {0.0, 0.0, 0.0, 0.0};
+    if (AUTO) team.template combine<4>(0, t4);
+    else team.template combine<3>(0, *reinterpret_cast<double(*)[3]>(t4));
     double t1[1];
     team.template combine<1>(1, t1);
-    rho = t3[0];
+    rho = t4[0];
     rw0 = t1[0];
     PBCG_BCAST_BEGIN
-      sc[0] = sqrt(t3[1]);
+      sc[0] = sqrt(t4[1]);
       sc[1] = sqrt(rho);
       sc[2] = rw0 != 0.0 ? rho / rw0 : INFINITY;
       sc[3] = p.tol * sc[0];
-      if (AUTO) gb_start(gb, p, sqrt(t3[2]), sc[0], sc[1]);
+      sc[4] = sqrt(t4[2]);
+      if (AUTO) gb_start(gb, p, sqrt(t4[3]), sc[0], sc[1]);
     PBCG_BCAST_END
     bn = sc[0];
     rn = sc[1];
     alpha = sc[2];
     tolb = sc[3];
+    rtrue = sc[4];
     PBCG_BCAST_DONE
   }
   if (first) {
@@ -527,18 +744,37 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
     rn0 = rn;
     first = false;
   }
-  if (rn <= tolb) PBCG_FINISH(kOK, it, rn);
+  if (rtrue <= tolb) PBCG_FINISH(kOK, it, rn);
+  if (p.stag_window > 0) {
+    // reading R21: progress of the FP64 true residual between (re)starts
+    if (rtrue <= 0.5 * ref_true) {
+      ref_true = rtrue;
+      ref_it = it;
+    } else if (it - ref_it >= p.stag_window) {
+      if (p.xbest && best_true < rtrue) PBCG_ROWS { p.x[i] = p.xbest[i]; }
+      PBCG_FINISH(kStagnated, it, rn);
+    }
+    if (rtrue < best_true) {   // each thread copies the rows it alone updates
+      best_true = rtrue;
+      if (p.xbest) PBCG_ROWS { p.xbest[i] = p.x[i]; }
+    }
+  }
   if (rw0 == 0.0 || !isfinite(alpha)) PBCG_FINISH(kBreakdown, it, rn);
+  const int it_start = it;
   double beta = 0.0, omega_prev = 0.0;
   bool rep_last = false;
   bool restart = false;
-  const double sqrt_eps = 1.4901161193847656e-08;  // sqrt(2^-52)
-  const double rr_cutoff = sqrt_eps * rn0;          // periodic replacements stop below this
+  // interior rows of this block, and whether t = A m was computed on them inside the last
+  // barrier (never right after a (re)start or a replacement forced by the stop test)
+  const Interior inner = interior_of(p, team);
+  const Interior none{0, 0, 0};
+  bool t_pre = false;
+  const double rr_cutoff = p.rr_cutoff * rn0;       // periodic replacements stop below this
   double rr_theta_thr = p.rr_theta * rn;            // relative trigger threshold
 
   for (; it < p.max_it; ++it) {
     // ---------------- m_i = M^{-1} w_i (Neumann only; on the fly otherwise)
-    if (neu && !neumann_apply(p, team, p.w, p.m, (const T*)nullptr, (T*)nullptr)) return;
+    if (neu && !neumann_apply<VEC>(p, team, p.w, p.m, (const T*)nullptr, (T*)nullptr)) return;
     // ---------------- pass A: t_i = A m_i; g, s, l, z, q, u, y; partials of (q, y), (y, y)
     const bool split = team.lanes > 1 && !neu && p.At.fmt == 0;   // lane-split SpMVs (batched CSR)
     if (split) spmv_lanes(team, p.At, p.w, p.t);
@@ -546,16 +782,18 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       const T aT = T(alpha), bT = T(beta), opT = T(omega_prev);
       Acc a_qy, a_yy;
       Acc an[12];   // AUTO: squared norms of r k w g s l z q u y m t (iteration i)
-      PBCG_ROWS {
-        if (p.prefetch && i + rstride < row1) {   // the next row's operands, into L2 while this row computes
-          const int j = i + rstride;
+      const Interior& tin = t_pre ? inner : none;
+      if constexpr (VEC) pass_a_quads<SCALAR>(p, team, aT, bT, opT, rep_last, tin, a_qy, a_yy);
+      else PBCG_ROWS {
+        if (p.prefetch && i + p.prefetch * rstride < row1) {   // operands of a later row, into L2
+          const int j = i + p.prefetch * rstride;
           prefetch_l2(p.w + j); prefetch_l2(p.z + j); prefetch_l2(p.k + j); prefetch_l2(p.g + j);
           prefetch_l2(p.l + j); prefetch_l2(p.s + j); prefetch_l2(p.v + j); prefetch_l2(p.r + j);
           if (neu) { prefetch_l2(p.m + j); prefetch_l2(p.nn + j); }
         }
         const T wi = p.w[i];
         const T mi = neu ? p.m[i] : minv_local<SCALAR>(p, wi, i);
-        const T ti = split ? p.t[i] : neu ? row_dot<T>(p.Au, p.m, i) : row_dot<T>(p.At, p.w, i);
+        const T ti = (split || tin.row(i)) ? p.t[i] : neu ? row_dot<T>(p.Au, p.m, i) : row_dot<T>(p.At, p.w, i);
         const T zo = p.z[i];
         const T np = neu ? p.nn[i] : (rep_last ? p.nb[i] : minv_local<SCALAR>(p, zo, i));   // n_{i-1}
         const T kk = p.k[i], gg = p.g[i], ll = p.l[i], ss = p.s[i], vv = p.v[i], rr = p.r[i];
@@ -587,9 +825,19 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         team.template publish<2>(v2, 0);
       }
     }
-    PBCG_SYNC();
+    if constexpr (std::is_same<Team, GridTeam>::value) {
+      if (p.overlap) {   // v_i = A n_i on the interior rows while the first reduction completes
+        team.arrive();
+        interior_product<VEC>(p, team, inner, p.z, p.v);
+        if (!team.wait()) return;
+      } else {
+        PBCG_SYNC();
+      }
+    } else {
+      PBCG_SYNC();
+    }
     // ---------------- n_i = M^{-1} z_i (Neumann only), overlapping the reduction
-    if (neu && !neumann_apply(p, team, p.z, p.nn, (const T*)nullptr, (T*)nullptr)) return;
+    if (neu && !neumann_apply<VEC>(p, team, p.z, p.nn, (const T*)nullptr, (T*)nullptr)) return;
     double omega;
     bool do_auto = false;
     {
@@ -625,9 +873,11 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       DAcc a_xn;
       Acc a_nn, a_vn;   // AUTO: squared norms of x_i, n_i, v_i
       const bool hist = it < p.K;
-      PBCG_ROWS {
-        if (p.prefetch && i + rstride < row1) {
-          const int j = i + rstride;
+      if constexpr (VEC)
+        pass_b_quads<SCALAR>(p, team, aT, oT, ax, ox, hist, it, do_rr, inner, a_rr, a_rw, a_rs, a_rz, a_r2);
+      else PBCG_ROWS {
+        if (p.prefetch && i + p.prefetch * rstride < row1) {
+          const int j = i + p.prefetch * rstride;
           prefetch_l2(p.z + j); prefetch_l2(p.w + j); prefetch_l2(p.r + j); prefetch_l2(p.s + j);
           prefetch_l2(p.k + j); prefetch_l2(p.l + j); prefetch_l2(p.g + j); prefetch_l2(p.t + j);
           prefetch_l2(p.x + j); prefetch_l2(p.rh + j);
@@ -635,7 +885,7 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
         }
         const T zi = p.z[i];
         const T ni = neu ? p.nn[i] : minv_local<SCALAR>(p, zi, i);
-        const T vi = split ? p.v[i] : neu ? row_dot<T>(p.Au, p.nn, i) : row_dot<T>(p.At, p.z, i);
+        const T vi = (split || inner.row(i)) ? p.v[i] : neu ? row_dot<T>(p.Au, p.nn, i) : row_dot<T>(p.At, p.z, i);
         const T wi = p.w[i];
         const T mi = neu ? p.m[i] : minv_local<SCALAR>(p, wi, i);
         const T rr = p.r[i], ss = p.s[i], kk = p.k[i], ll = p.l[i], gg = p.g[i], ti = p.t[i];
@@ -673,7 +923,19 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       ++nrep;
     }
     rep_last = do_rr;
-    PBCG_SYNC();
+    t_pre = false;
+    if constexpr (std::is_same<Team, GridTeam>::value) {
+      if (p.overlap) {   // t_{i+1} = A m_{i+1} on the interior rows while the second reduction completes
+        team.arrive();
+        interior_product<VEC>(p, team, inner, p.w, p.t);
+        if (!team.wait()) return;
+        t_pre = true;
+      } else {
+        PBCG_SYNC();
+      }
+    } else {
+      PBCG_SYNC();
+    }
     // ---------------- second reduction, stopping test, beta_{i+1}, alpha_{i+1}
     double t5[6];
     if (AUTO && do_rr) team.template combine<6>(1, t5);
@@ -717,12 +979,16 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
           double* h = p.hist_s + (size_t)it * PBCG_HS;
           h[0] = alpha; h[1] = omega; h[2] = NAN; h[3] = rn / bn; h[4] = do_rr ? 1.0 : 0.0;
         }
+        if (true_rn > tolb && p.restart_period > 0) {   // reading R20: restart from x instead
+          ++nperiodic; ++it; restart = true; break;
+        }
         PBCG_FINISH(true_rn <= tolb ? kOK : kStagnated, it + 1, rn);
       }
       if (!replace_r2<AUTO>(p, team)) return;
       ++nrep;
       rep_last = true;
       do_rr = true;
+      t_pre = false;   // w was replaced after t was computed from it
       PBCG_SYNC();
       if (AUTO) team.template combine<6>(1, t5);
       else team.template combine<5>(1, *reinterpret_cast<double(*)[5]>(t5));
@@ -760,12 +1026,31 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
       if (nrestart < p.max_restarts) { ++nrestart; ++it; restart = true; break; }
       PBCG_FINISH(kBreakdown, it + 1, rn);
     }
+    if (p.restart_period > 0 && it + 1 - it_start >= p.restart_period) {   // reading R20
+      ++nperiodic; ++it; restart = true; break;
+    }
     alpha = alpha_new;
     beta = beta_new;
     omega_prev = omega;
     rho = rho_new;
   }
-  if (!restart) PBCG_FINISH(kNotConverged, p.max_it, rn);
+  if (!restart) {
+    if (p.stag_window > 0 && p.xbest && best_true < INFINITY) {
+      // reading R21: return the best (re)start iterate when the last one is worse
+      replace_r1<AUTO, SCALAR>(p, team, false);
+      PBCG_SYNC();
+      double t6[6];
+      if (AUTO) team.template combine<6>(2, t6);
+      else team.template combine<1>(2, *reinterpret_cast<double(*)[1]>(t6));
+      PBCG_BCAST_BEGIN
+        sc[0] = sqrt(t6[0]);
+      PBCG_BCAST_END
+      const double last_true = sc[0];
+      PBCG_BCAST_DONE
+      if (best_true < last_true) PBCG_ROWS { p.x[i] = p.xbest[i]; }
+    }
+    PBCG_FINISH(kNotConverged, p.max_it, rn);
+  }
   }  // restarts
 #undef PBCG_SYNC
 #undef PBCG_ROWS
@@ -782,16 +1067,20 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
 // by memory-level parallelism, so STREAM trades registers (40, with some spilling) for 48
 // resident warps per SM (three 512-thread blocks): 1173 vs 1301 us per iteration on the
 // 256^3 Neumann system (FP64 at that budget loses 12%).
-template <typename T, bool STREAM>
+template <typename T, bool STREAM, bool VEC = false>
 struct SolverLaunch {
-  static constexpr int kThreads = STREAM ? 512 : kMaxThreads;
-  static constexpr int kBlocksPerSM = STREAM ? 3 : 1;
+  static constexpr int kThreads = VEC ? 512 : STREAM ? 512 : kMaxThreads;
+  static constexpr int kBlocksPerSM = VEC ? 1 : STREAM ? 3 : 1;
 };
 
 // One cooperative grid solves one system.  AUTO adds the automated replacement policy
 // (extra norms in the reductions and the gap bound in thread 0).
-template <typename T, bool AUTO, bool STREAM = false, bool SCALAR = false>
-__global__ void __launch_bounds__(SolverLaunch<T, STREAM>::kThreads, SolverLaunch<T, STREAM>::kBlocksPerSM)
+// VEC: the hot passes take four rows per thread (structured-stencil storage, n a multiple
+// of 4, 16-byte aligned vectors, p.chunk a multiple of 4); the other passes keep one row
+// per thread -- every pass is separated from the next by a barrier, so the two row
+// mappings never meet inside one.
+template <typename T, bool AUTO, bool STREAM = false, bool SCALAR = false, bool VEC = false>
+__global__ void __launch_bounds__(SolverLaunch<T, STREAM, VEC>::kThreads, SolverLaunch<T, STREAM, VEC>::kBlocksPerSM)
     pbicgstab_kernel(const SolverParams<T> p) {
   __shared__ double smem[kWork + 3 * kMaxDots];
   __shared__ double scal[8];
@@ -802,10 +1091,14 @@ __global__ void __launch_bounds__(SolverLaunch<T, STREAM>::kThreads, SolverLaunc
     team.first = blockIdx.x * blockDim.x;
     team.stride = gridDim.x * blockDim.x;
     team.end = p.n;
+    team.first4 = 4 * blockIdx.x * blockDim.x;
+    team.stride4 = 4 * gridDim.x * blockDim.x;
   } else {
     team.first = (int)min((long long)p.n, (long long)blockIdx.x * p.chunk);
     team.stride = blockDim.x;
     team.end = min(p.n, team.first + p.chunk);
+    team.first4 = team.first;
+    team.stride4 = 4 * blockDim.x;
   }
   team.epoch = 0;
   team.bar = p.bar;
@@ -814,7 +1107,7 @@ __global__ void __launch_bounds__(SolverLaunch<T, STREAM>::kThreads, SolverLaunc
   team.part = p.part;
   team.smem = smem;
   team.scal = scal;
-  solve_body<AUTO, SCALAR>(p, team);
+  solve_body<AUTO, SCALAR, VEC>(p, team);
 }
 
 // Several independent solves that share the grid: team t is blocks

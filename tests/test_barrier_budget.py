@@ -15,8 +15,8 @@ SOURCE = r"""
 #include <cstring>
 #include "capi_internal.h"
 
-static int ok(int max_it, int restarts, int degree, int blocks) {
-  return check_barrier_budget(max_it, restarts, degree, blocks) == PBCG_OK;
+static int ok(int max_it, int restarts, int degree, int blocks, int restart_period = 0, int stag = 0) {
+  return check_barrier_budget(max_it, restarts, degree, blocks, restart_period, stag) == PBCG_OK;
 }
 
 int main() {
@@ -36,6 +36,18 @@ int main() {
     long long lim = 0;
     if (sscanf(at + 8, "%lld", &lim) != 1 || lim < 1) return 6;
     if (!ok((int)lim, c[1], c[0], c[2]) || ok((int)lim + 1, c[1], c[0], c[2])) return 7;
+  }
+  // with a restart policy (restart every 75 iterations, stagnation window): the benchmark's
+  // mixed 2D solve (304 blocks of the four-row kernel) and 3D solves are accepted
+  if (!ok(20000, 0, 0, 304, 75, 4000) || !ok(20000, 0, 2, 152, 100, 4000)) return 8;
+  // a restart policy costs up to one (re)start per iteration, so its limit is lower
+  {
+    if (check_barrier_budget(2147483647, 0, 2, 152, 100, 1) != PBCG_INVALID_ARG) return 9;
+    const char* at = strstr(pbicgstab_last_error(), "at most ");
+    long long lim = 0;
+    if (!at || sscanf(at + 8, "%lld", &lim) != 1 || lim < 1) return 10;
+    if (!ok((int)lim, 0, 2, 152, 100, 1) || ok((int)lim + 1, 0, 2, 152, 100, 1)) return 11;
+    if (!ok((int)lim + 1, 0, 2, 152, 0, 0)) return 12;   // without restarts the same max_it fits
   }
   printf("ok\n");
   return 0;

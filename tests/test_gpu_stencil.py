@@ -56,12 +56,15 @@ CASES = {
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_solves_bitwise_equal_to_general_storage(name):
+    """Same kernel, same launch shape: 1024-thread blocks keep the stencil context on the
+    one-row kernels (the four-row ones sum the dot products in another order), so the
+    stencil storage must reproduce the general storage bit for bit."""
     maker, fmt, precision, method, kw = CASES[name]
     prob = maker()
     out = []
     for storage in ("auto", "general"):
         s = make_solver(prob, fmt=fmt, precision=precision, method=method, tol=1e-10, max_it=3000,
-                        operator_storage=storage, **kw)
+                        operator_storage=storage, block_threads=1024, **kw)
         assert s.storage == ("stencil" if storage == "auto" else "general")
         x, res, its, hist = gpu_solve(s, prob.b, K=5, hist_len=50)
         out.append((x, res, its, hist))
@@ -91,3 +94,22 @@ def test_storage_fixed_at_create():
     s = make_solver(tp.problem_convdiff2d(20), fmt="dia")
     with pytest.raises(pb.PBCGError):
         s.set_options(operator_storage="general")
+
+
+def test_four_row_kernels_run_where_they_apply():
+    """Stencil storage, n a multiple of 4, aligned vectors and the default block size: the
+    four-row kernels; a ragged n, 1024-thread blocks or general storage: the one-row ones."""
+    prob = tp.problem_convdiff2d(64)                     # n = 4096
+    s = make_solver(prob, fmt="dia", tol=1e-10, max_it=500)
+    _, res, _, _ = gpu_solve(s, prob.b)
+    assert res.status == 0 and s.launch_info()["rows_per_thread"] == 4
+    s = make_solver(prob, fmt="dia", tol=1e-10, max_it=500, block_threads=1024)
+    gpu_solve(s, prob.b)
+    assert s.launch_info()["rows_per_thread"] == 1
+    s = make_solver(prob, fmt="dia", tol=1e-10, max_it=500, operator_storage="general")
+    gpu_solve(s, prob.b)
+    assert s.launch_info()["rows_per_thread"] == 1
+    ragged = tp.problem_convdiff2d(63)                   # n = 3969
+    s = make_solver(ragged, fmt="dia", tol=1e-10, max_it=500)
+    _, res, _, _ = gpu_solve(s, ragged.b)
+    assert res.status == 0 and s.launch_info()["rows_per_thread"] == 1

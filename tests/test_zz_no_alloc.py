@@ -53,8 +53,12 @@ CASES = [("convdiff2d_128_dia_jacobi_rr", lambda: tp.problem_convdiff2d(128), "d
          ("convdiff2d_90_csr_jacobi_ragged", lambda: tp.problem_convdiff2d(90), "csr", "jacobi", dict(rr_period=50))]
 
 
+@pytest.mark.parametrize("threads", [512, 0], ids=["fixed_512_threads", "default_shape"])
 @pytest.mark.parametrize("name,maker,fmt,prec,kw", CASES)
-def test_noalloc_matches_context_solver_twice(name, maker, fmt, prec, kw):
+def test_noalloc_matches_context_solver_twice(name, maker, fmt, prec, kw, threads):
+    """threads = 0 leaves the launch shape to each entry point: both use the same default
+    rule for a matrix kept as given (this entry point never uses the stencil storage), so
+    they sum the dot products in the same order."""
     torch, pb, capi, lib = _setup()
     dev = torch.device("cuda:0")
     prob = maker()
@@ -65,7 +69,8 @@ def test_noalloc_matches_context_solver_twice(name, maker, fmt, prec, kw):
                                  dict(row_ptr=torch.from_numpy(prob.A.row_ptr).to(dev),
                                       col=torch.from_numpy(prob.A.col).to(dev),
                                       val=torch.from_numpy(prob.A.val).to(dev))),
-                    precond=prec, precision="fp64", tol=tol, max_it=5000, block_threads=512, **kw)
+                    precond=prec, precision="fp64", tol=tol, max_it=5000, block_threads=threads,
+                    operator_storage="general", **kw)
     b = torch.from_numpy(prob.b).to(dev)
     x_ref, r_ref = ref.solve(b)
     x_ref = x_ref.cpu().numpy()
@@ -75,7 +80,7 @@ def test_noalloc_matches_context_solver_twice(name, maker, fmt, prec, kw):
     opt = capi.Options()
     lib.pbicgstab_default_options(C.byref(opt))
     opt.tol, opt.max_it = tol, 5000
-    opt.block_threads = 512   # the same launch shape as the context above (same reduction order)
+    opt.block_threads = threads   # the same launch shape as the context above (same reduction order)
     opt.rr_period = kw.get("rr_period", 0)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     for call in range(2):
