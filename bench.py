@@ -1,16 +1,17 @@
-"""Benchmark: p-BiCGStab time to a 1e-10 true relative residual on GB300.
+"""Benchmark: p-BiCGStab time to a 1e-10 true relative residual on GB300, mixed vs FP64.
 
-Workload (one "step" = one complete solve): 2D upwind convection-diffusion,
-1024 x 1024 grid (N = 1,048,576), cell Peclet 0.5, matrix stored as 5 FP64
-diagonals, Jacobi preconditioner, x* ~ U[0,1] (seed 2), b = A x*, x0 = 0,
-tol 1e-10 on ||b - A x|| / ||b||.  The headline variant is set by --precision
-(fp64 with periodic replacement every 100 iterations by default); the other
-variants (mixed precision, and on the 2D workload classic BiCGStab, Algorithm 1)
-are measured alongside.
+Headline workload (one "step" = one complete solve): 2D upwind convection-diffusion,
+1024 x 1024 grid (N = 1,048,576), cell Peclet 0.5, matrix stored as 5 FP64 diagonals,
+Jacobi preconditioner, x* ~ U[0,1] (seed 2), b = A x*, x0 = 0, tol 1e-10 on
+||b - A x|| / ||b|| (verified in FP64).  The headline variant is set by --precision:
+mixed (FP32 recurrences restarted from the FP64 residual every 75 iterations, the
+default) or fp64; the FP64 variants (the same restart policy, the paper's periodic
+replacement, and classic BiCGStab, Algorithm 1) are measured alongside.  The 3D
+256^3 CSR system with the degree-2 Neumann preconditioner (N = 16,777,216) is measured
+in the same run ("convdiff3d" block; --no-3d skips it).
 
-Prints ONE JSON line on rank 0.  --impl reference times the CPU oracle instead
-(a bounded sample of iterations, extrapolated with the oracle's iteration count
-stored in tests/golden/oracle_iterations_convdiff2d_1024.json).
+Prints ONE JSON line on rank 0.  --impl reference times the oracle instead: the same
+headline solve, run to completion by the C oracle on all host cores.
 """
 from __future__ import annotations
 
@@ -27,7 +28,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "p-BiCGStab time to true rel. residual 1e-10 & HBM GB/s, mixed vs FP64"
 GRID = 1024
-GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations_convdiff2d_1024.json")
 
 
 # ----------------------------------------------------------------------------- byte model
@@ -103,7 +103,8 @@ def fp64_flops_per_row_iteration_neumann(nnz_row: int = 7, degree: int = 2) -> f
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("common.cuh", "solver.cuh", "capi.cu", "capi_internal.h", "stencil.cu"):
+    for f in ("common.cuh", "solver.cuh", "capi.cu", "capi_internal.h", "stencil.cu", "kernels_f64.cu",
+              "kernels_f32.cu", "kernels_vec.cu"):
         h.update(open(os.path.join(ROOT, "paper_1809_01948_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -173,10 +174,110 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def bytes_per_row_restart(precision: str, ndiag: int = 5, storage: str = "stencil") -> float:
+    """A (re)start of Algorithm 2 (reading R20): the initialisation pass reads b, x and the FP64
+    operator, writes r, r0, k and zeros g, s, l, z, v; the next pass reads k and the operator
+    and writes w."""
+    es = 8 if precision == "fp64" else 4
+    op64 = MASK_BYTES if storage == "stencil" else ndiag * 8
+    opT = MASK_BYTES if storage == "stencil" else ndiag * es
+    return float(2 * 8 + op64 + 8 * es + es + opT + es)
+
+
+def measured_fp64_tflops(dev) -> float:
+    """FP64 arithmetic rate of this GPU, measured here: a cuBLAS DGEMM (4096^3, best of 5,
+    CUDA events) -- the denominator of the FP64-pipe roofline."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b_ = torch.randn(n, n, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        torch.matmul(a, b_)
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b_)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b_
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def workload_setup(kind: str, grid: int, dev):
+    """The synthetic system of a workload, its solver inputs, and the byte / flop models."""
+    import torch
+    import testproblems as tp
+    if kind == "convdiff2d":
+        prob = tp.problem_convdiff2d(grid)
+        off, data = tp.csr_to_dia(prob.A)
+        mat = dict(offsets=off.tolist(), dia=torch.from_numpy(data).to(dev), precond="jacobi")
+        name = "convdiff2d_%dx%d_dia5_jacobi_tol1e-10" % (grid, grid)
+        fmt = "DIA 5 diagonals FP64"
+        variants = {
+            # FP32 recurrences restarted from the FP64 residual every 75 iterations (reading R20)
+            "mixed": dict(precision="mixed", restart_period=75, stag_window=4000),
+            # FP64 with the same restart policy (every 200 iterations)
+            "fp64": dict(precision="fp64", restart_period=200, stag_window=4000),
+            # the paper's periodic residual replacement (Section 3.6, every 100 iterations)
+            "fp64_rr100": dict(precision="fp64", rr_period=100),
+            # Algorithm 1, the paper's reference method
+            "classic": dict(precision="fp64", method="classic"),
+        }
+        model = dict(bpr=lambda prec, st: bytes_per_row_iteration(prec, storage=st),
+                     flops=fp64_flops_per_row_iteration())
+    else:
+        prob = tp.problem_convdiff3d(grid)
+        mat = dict(row_ptr=torch.from_numpy(prob.A.row_ptr).to(dev), col=torch.from_numpy(prob.A.col).to(dev),
+                   val=torch.from_numpy(prob.A.val).to(dev), precond="neumann", degree=2)
+        name = "convdiff3d_%d^3_csr7_neumann2_tol1e-10" % grid
+        fmt = "CSR int32, 7 nnz/row, FP64 values"
+        variants = {
+            "mixed": dict(precision="mixed", rr_theta=3e-3),
+            "fp64": dict(precision="fp64", rr_period=100),
+        }
+        model = dict(bpr=lambda prec, st: bytes_per_row_iteration_neumann(prec, storage=st),
+                     flops=fp64_flops_per_row_iteration_neumann())
+    return prob, mat, name, fmt, variants, model
+
+
+def roofline_of(kind, model, prec, res, n, hbm_peak, hbm_src, fp64_peak, storage, workload):
+    """Roofline of the persistent solver kernel (one launch per solve) from its CUDA-event
+    time: achieved algorithmic bytes (the section 8(d) model: matrix values as stored by the
+    general formats) and the same with the stencil storage's actual operand set, DRAM traffic
+    from the ncu table, and for FP64 the FP64-pipe rate against the measured DGEMM peak."""
+    its, nrep, nrst = res["iterations"], res["n_replacements"], res["n_restarts"]
+    kernel_s = res["kernel_ms"] * 1e-3
+
+    def gbs(st):
+        b = n * (model["bpr"](prec, st) * its + bytes_per_row_replacement(prec, storage=st) * nrep
+                 + bytes_per_row_restart(prec, storage=st) * nrst)
+        return b / kernel_s / 1e9
+
+    per_it = measured_traffic(prec, workload)
+    hbm = {"achieved": round(gbs("general"), 1), "peak": hbm_peak, "unit": "GB/s",
+           "frac": round(gbs("general") / hbm_peak, 4), "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)",
+           "model": "section 8(d) algorithmic bytes: %.0f B per row and iteration" % model["bpr"](prec, "general"),
+           "traffic": per_it * its if per_it is not None else None,
+           "stencil_storage_model": {"bytes_per_row_iteration": model["bpr"](prec, "stencil"),
+                                     "achieved": round(gbs("stencil"), 1),
+                                     "frac": round(gbs("stencil") / hbm_peak, 4)} if storage == "stencil" else None}
+    if prec == "fp64":
+        ach = model["flops"] * n * its / kernel_s / 1e12
+        return {"bound": "alu", "achieved": round(ach, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                "frac": round(ach / fp64_peak, 4), "traffic": hbm["traffic"],
+                "peak_source": "measured in this run (cuBLAS DGEMM 4096^3, FP64 pipe)",
+                "flops_per_row_iteration": model["flops"], "hbm": hbm}
+    out = {"bound": "hbm"}
+    out.update(hbm)
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
-    import testproblems as tp
     import paper_1809_01948_gb300 as pb
     from paper_1809_01948_gb300.sharding import max_over_ranks
     pb.build()
@@ -189,80 +290,79 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-
-    if args.workload == "convdiff2d":
-        prob = tp.problem_convdiff2d(args.grid or GRID)
-        off, data = tp.csr_to_dia(prob.A)
-        mat = dict(offsets=off.tolist(), dia=torch.from_numpy(data).to(dev), precond="jacobi")
-        workload = "convdiff2d_%dx%d_dia5_jacobi_tol1e-10" % ((args.grid or GRID), (args.grid or GRID))
-    else:
-        prob = tp.problem_convdiff3d(args.grid or 256)
-        mat = dict(row_ptr=torch.from_numpy(prob.A.row_ptr).to(dev), col=torch.from_numpy(prob.A.col).to(dev),
-                   val=torch.from_numpy(prob.A.val).to(dev), precond="neumann", degree=2)
-        workload = "convdiff3d_%d^3_csr7_neumann2_tol1e-10" % (args.grid or 256)
-    b = torch.from_numpy(prob.b).to(dev)
-    n = prob.A.n
-    variants = {
-        "fp64": dict(precision="fp64", rr_period=100, rr_theta=0.0),
-        "mixed": dict(precision="mixed", rr_period=args.mixed_period, rr_theta=args.theta),
-    }
-    if args.workload == "convdiff2d":
-        # Algorithm 1, the paper's reference method, on the same system (three reduction
-        # phases per iteration instead of two)
-        variants["classic"] = dict(precision="fp64", method="classic", rr_period=0, rr_theta=0.0)
-        # the relative replacement trigger instead of the period (fewer replacements)
-        variants["fp64_theta"] = dict(precision="fp64", rr_period=0, rr_theta=1e-3)
-    # the headline variant with the matrix values kept as given (CSR / DIA) instead of the
-    # constant-coefficient stencil storage the library selects for these operators
-    variants[args.precision + "_general"] = dict(variants[args.precision], operator_storage="general")
-    solvers = {k: pb.Solver(n, tol=1e-10, max_it=args.max_it, **mat, **v) for k, v in variants.items()}
-    storage = solvers[args.precision].storage
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
+    hbm_peak, hbm_src = _hbm_peak()
+    fp64_peak = measured_fp64_tflops(dev)
+    sampler = ClockSampler(args.clocks_csv)
+    sampler_on = False
 
-    def one(name):
-        x = torch.zeros(n, dtype=torch.float64, device=dev)
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        x, res = solvers[name].solve(b, x)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1), res, x
+    def measure(kind, grid, headline):
+        nonlocal sampler_on
+        prob, mat, name, fmt, variants, model = workload_setup(kind, grid, dev)
+        b = torch.from_numpy(prob.b).to(dev)
+        n = prob.A.n
+        if args.only:
+            variants = {headline: variants[headline]}
+        solvers = {k: pb.Solver(n, tol=1e-10, max_it=args.max_it, **mat, **v) for k, v in variants.items()}
+        storage = solvers[headline].storage
 
-    results = {}
-    clocks = None
-    order = (args.precision,) + (() if args.only else tuple(k for k in variants if k != args.precision))
-    for name in order:
-        for _ in range(args.warmup):
-            one(name)
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        sampler = ClockSampler(args.clocks_csv) if name == args.precision else None
-        if sampler:
-            sampler.start()
-        times, ktimes, its, nrep, trues, stat = [], [], [], [], [], []
-        for _ in range(args.steps):
-            ms, res, x = one(name)
-            times.append(ms)
-            ktimes.append(res.time_ms)
-            its.append(res.iterations)
-            nrep.append(res.n_replacements)
-            trues.append(res.rel_res_true)
-            stat.append(res.status)
-        torch.cuda.synchronize()
-        if sampler:
-            clocks = sampler.stop()
-        total = max_over_ranks(sum(times), device=dev)   # replicas: the slowest rank's time
-        results[name] = dict(ms_per_solve=total / args.steps, kernel_ms=statistics.mean(ktimes),
-                             iterations=its[-1], n_replacements=nrep[-1], rel_res_true=max(trues),
-                             status=[pb.STATUS_NAMES[s] for s in stat][-1])
+        def one(vname):
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, res = solvers[vname].solve(b, x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), res
+
+        results = {}
+        for vname in [headline] + [k for k in variants if k != headline]:
+            for _ in range(args.warmup):
+                one(vname)
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            if not sampler_on:
+                sampler.start()
+                sampler_on = True
+            times, ktimes, last = [], [], None
+            for _ in range(args.steps):
+                ms, res = one(vname)
+                times.append(ms)
+                ktimes.append(res.time_ms)
+                last = res
+            torch.cuda.synchronize()
+            total = max_over_ranks(sum(times), device=dev)   # replicas: the slowest rank's time
+            r = dict(ms_per_solve=round(total / args.steps, 4), kernel_ms=round(statistics.mean(ktimes), 4),
+                     iterations=last.iterations, n_replacements=last.n_replacements, n_restarts=last.n_restarts,
+                     rel_res_true=last.rel_res_true, status=pb.STATUS_NAMES[last.status],
+                     policy=variants[vname])
+            prec = variants[vname]["precision"]
+            r["roofline"] = roofline_of(kind, model, prec, r, n, hbm_peak, hbm_src, fp64_peak,
+                                        solvers[vname].storage, name)
+            results[vname] = r
+        return dict(prob=prob, n=n, name=name, fmt=fmt, storage=storage, results=results, solvers=solvers,
+                    variants=variants)
+
+    headline = args.precision
+    third = None
+    if args.workload == "convdiff3d":          # the 3D system alone, as the headline
+        main = measure("convdiff3d", args.grid3 or 256, headline)
+    else:
+        main = measure("convdiff2d", args.grid or GRID, headline)
+        if not args.no_3d:
+            third = measure("convdiff3d", args.grid3 or 256, headline)
+            for s_ in third["solvers"].values():
+                s_.close()
+    clocks = sampler.stop() if sampler_on else None
+    head = main["results"][headline]
+    n = main["n"]
 
     # end-to-end through the public API with host buffers (pinned)
-    head = results[args.precision]
-    b_pin = torch.from_numpy(prob.b).pin_memory()
+    b_pin = torch.from_numpy(main["prob"].b).pin_memory()
     x_pin = torch.zeros(n, dtype=torch.float64).pin_memory()
     e2e_times = []
     for k in range(0 if args.no_e2e else max(1, args.steps)):
@@ -270,77 +370,57 @@ def run_gpu(args):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, res = solvers[args.precision].solve_host(b_pin.numpy(), x_pin.numpy())
+        _, res = main["solvers"][headline].solve_host(b_pin.numpy(), x_pin.numpy())
         e2e_times.append((time.perf_counter() - t0) * 1e3)
-    e2e = {"value": statistics.mean(e2e_times) if e2e_times else None, "unit": "ms", "h2d_bytes_per_step": 2 * 8 * n,
-           "d2h_bytes_per_step": 8 * n + 64}
+    e2e = {"value": round(statistics.mean(e2e_times), 4) if e2e_times else None, "unit": "ms",
+           "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n + 64}
+    for s_ in main["solvers"].values():
+        s_.close()
 
-    # roofline of the dominant kernel (the persistent solver), per launch
-    prec = args.precision
-    bpr = (bytes_per_row_iteration(prec, storage=storage) if args.workload == "convdiff2d"
-           else bytes_per_row_iteration_neumann(prec, storage=storage))
-    alg_bytes = n * (bpr * head["iterations"] + bytes_per_row_replacement(prec, storage=storage) * head["n_replacements"])
-    kernel_s = head["kernel_ms"] * 1e-3
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    per_it = measured_traffic(prec, workload)
-    traffic = per_it * head["iterations"] if per_it is not None else None
-    hbm = {"achieved": round(alg_bytes / kernel_s / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",
-           "frac": round(alg_bytes / kernel_s / 1e9 / hbm_peak, 4),
-           "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-           "bytes_per_row_iteration": bpr}
-    # the same time against the byte model of the general (CSR / DIA values) storage, which
-    # the stencil storage undercuts: the effective bandwidth of the solve
-    gen = (bytes_per_row_iteration(prec, storage="general") if args.workload == "convdiff2d"
-           else bytes_per_row_iteration_neumann(prec, storage="general"))
-    gen_bytes = n * (gen * head["iterations"] + bytes_per_row_replacement(prec, storage="general") * head["n_replacements"])
-    hbm["general_storage_model"] = {"bytes_per_row_iteration": gen,
-                                    "effective_gbs": round(gen_bytes / kernel_s / 1e9, 1),
-                                    "frac": round(gen_bytes / kernel_s / 1e9 / hbm_peak, 4)}
-    if prec == "fp64":
-        # FP64 pipe bound: GB300 runs FP64 at 1/58 of FP32; nominal 1.25 TFLOP/s (measured DFMA 1.197)
-        fpr = fp64_flops_per_row_iteration() if args.workload == "convdiff2d" else fp64_flops_per_row_iteration_neumann()
-        ach = fpr * n * head["iterations"] / kernel_s / 1e12
-        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": 1.25, "unit": "TFLOP/s",
-                "frac": round(ach / 1.25, 4), "traffic": traffic,
-                "peak_source": "nominal FP64 rate of the profiling recipe (measured DFMA: 1.197)",
-                "flops_per_row_iteration": fpr, "hbm": hbm}
-    else:
-        roof = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": hbm["frac"], "traffic": traffic, "peak_source": hbm["peak_source"],
-                "bytes_per_row_iteration": bpr, "general_storage_model": hbm["general_storage_model"],
-                }
-        if args.workload == "convdiff2d":
-            roof["note"] = "working set is L2-resident across iterations (DRAM traffic ~3 B/row/it)"
+    def block(m):
+        res = m["results"]
+        out = {"config": {"workload": m["name"], "n": m["n"], "format": m["fmt"],
+                          "operator_storage": m["storage"]},
+               "variants": {k: {kk: vv for kk, vv in v.items() if kk != "roofline"} for k, v in res.items()},
+               "rooflines": {k: v["roofline"] for k, v in res.items()}}
+        if "mixed" in res and "fp64" in res:
+            out["mixed_vs_fp64"] = round(res["fp64"]["ms_per_solve"] / res["mixed"]["ms_per_solve"], 3)
+        return out
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and args.workload == "convdiff2d":
-        cpu = cpu_baseline(args, head["iterations"], sample_iters=args.cpu_iters)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args)
 
     if rank == 0:
+        prec = main["variants"][headline]["precision"]
         line = {
-            "metric": METRIC, "value": round(head["ms_per_solve"], 4), "unit": "ms", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms_per_solve"], 4),
+            "metric": METRIC, "value": head["ms_per_solve"], "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_solve"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
-            "config": {"workload": workload, "n": n,
-                       "format": "DIA 5 diagonals FP64" if args.workload == "convdiff2d" else "CSR int32, 7 nnz/row, FP64 values",
-                       "operator_storage": storage + (" (constant coefficients detected at create: one value per "
-                                                      "offset + 16-bit row mask)" if storage == "stencil" else ""),
-                       "precision": prec, "replacement": variants[prec], "global_batch": 1 * world,
-                       "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps (256 MB write)"},
-            "iterations": head["iterations"], "n_replacements": head["n_replacements"],
-            "rel_res_true": head["rel_res_true"], "status": head["status"],
+            "config": {"workload": main["name"], "n": n, "format": main["fmt"],
+                       "operator_storage": main["storage"] + (
+                           " (constant coefficients detected at create: one value per offset + 16-bit row mask)"
+                           if main["storage"] == "stencil" else ""),
+                       "precision": prec + (" (FP32 vectors, values, SpMV and recurrences; FP64 x, dot products, "
+                                            "scalars, restart residual; true residual verified in FP64)"
+                                            if prec == "mixed" else ""),
+                       "policy": main["variants"][headline], "global_batch": 1 * world,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between steps (256 MB write)"},
+            "iterations": head["iterations"], "n_restarts": head["n_restarts"],
+            "n_replacements": head["n_replacements"], "rel_res_true": head["rel_res_true"],
+            "status": head["status"],
             "iters_per_s": round(head["iterations"] / (head["kernel_ms"] * 1e-3), 1),
-            "kernel_ms": round(head["kernel_ms"], 4),
-            "variants": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv) for kk, vv in v.items()}
-                         for k, v in results.items()},
-            "roofline": roof, "e2e": e2e, "clocks": clocks,
+            "kernel_ms": head["kernel_ms"],
+            "mixed_vs_fp64": block(main).get("mixed_vs_fp64"),
+            "variants": block(main)["variants"],
+            "variant_rooflines": block(main)["rooflines"],
+            "roofline": head["roofline"],
+            "convdiff3d": block(third) if third else None,
+            "e2e": e2e, "clocks": clocks,
             "gpu_launches": 3 * args.steps,
+            "fp64_peak_tflops": round(fp64_peak, 4),
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -349,49 +429,45 @@ def run_gpu(args):
 
 
 # ----------------------------------------------------------------------------- CPU oracle arm
-_ORACLE_SNIPPET = r"""
-import json, sys, time, os
-sys.path.insert(0, %(root)r)
-import numpy as np
-import testproblems as tp
-from oracle import krylov
-prob = tp.problem_convdiff2d(%(grid)d)
-A = prob.A.to_scipy()
-t0 = time.perf_counter()
-r = krylov.pbicgstab(A, prob.b, precond="jacobi", tol=1e-300, maxit=%(iters)d, rr_period=100)
-dt = time.perf_counter() - t0
-print(json.dumps({"seconds": dt, "iterations": r.iterations}))
-"""
+# The oracle timed on the host cores: the C oracle (oracle/c_oracle.c, OpenMP over every
+# core), which restates the numpy oracle step for step, runs the headline solve of the 2D
+# 1024^2 system to completion with the headline variant's policy.
+HEADLINE_POLICY = {
+    "mixed": dict(mixed=True, restart_period=75, stag_window=4000),
+    "fp64": dict(mixed=False, restart_period=200, stag_window=4000),
+}
 
 
-def _oracle_sample(iters: int):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", _ORACLE_SNIPPET % dict(root=ROOT, grid=GRID, iters=iters)],
-                         capture_output=True, text=True, env=env, timeout=900)
-    if out.returncode:
-        raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+def _c_oracle_solve(prec: str, grid: int = GRID):
+    import numpy as np
+    import testproblems as tp
+    from oracle import c_oracle
+    prob = tp.problem_convdiff2d(grid)
+    A = prob.A.to_scipy()
+    t0 = time.perf_counter()
+    x, r = c_oracle.pbicgstab(A, prob.b, precond="jacobi", tol=1e-10, maxit=20000, **HEADLINE_POLICY[prec])
+    dt = time.perf_counter() - t0
+    true = float(np.linalg.norm(prob.b - A @ x) / np.linalg.norm(prob.b))
+    return dict(seconds=dt, iterations=r["iterations"], status=r["status"], rel_res_true=true,
+                n_restarts=r["n_restarts"], n=prob.A.n)
 
 
-def _golden_iterations(default: int) -> int:
-    try:
-        return int(json.load(open(GOLDEN_ITERS))["fp64_rr100"]["iterations"])
-    except Exception:
-        return default
-
-
-def cpu_baseline(args, gpu_iterations: int, sample_iters: int = 40):
-    s = _oracle_sample(sample_iters)
-    per_it = s["seconds"] / s["iterations"]
-    iters = _golden_iterations(gpu_iterations)
-    return {"value": round(per_it * iters * 1e3, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": "%d iterations of the FP64 numpy oracle on the full 1024x1024 system (%.1f s), "
-                      "extrapolated to %d iterations" % (s["iterations"], s["seconds"], iters),
-            "ms_per_iteration": round(per_it * 1e3, 3), "host": _host()}
+def cpu_baseline(args):
+    """The headline solve by the C oracle on all host cores, run to completion."""
+    from oracle import c_oracle
+    s = _c_oracle_solve(args.precision, args.grid or GRID)
+    bpr = bytes_per_row_iteration("fp64" if args.precision == "fp64" else "mixed", storage="general")
+    return {"value": round(s["seconds"] * 1e3, 1), "unit": "ms", "cores": c_oracle.threads(), "kind": "oracle",
+            "sample": "one complete solve of the 2D %d^2 system to a 1e-10 true residual with the headline "
+                      "policy (%s) by the C oracle (OpenMP, all host cores): %d iterations, %s, true residual %.2e"
+                      % (args.grid or GRID, args.precision, s["iterations"], s["status"], s["rel_res_true"]),
+            "ms_per_iteration": round(s["seconds"] * 1e3 / max(1, s["iterations"]), 3),
+            "algorithmic_gbs": round(bpr * s["n"] * s["iterations"] / s["seconds"] / 1e9, 1),
+            "host_copy_gbs": round(c_oracle.host_copy_gbs(), 1), "host": _host()}
 
 
 def _host():
-    """The machine the CPU baseline ran on (the oracle itself uses one thread)."""
+    """The machine the CPU baseline ran on."""
     import platform
     return {"arch": platform.machine(), "logical_cpus": os.cpu_count()}
 
@@ -548,27 +624,34 @@ def run_autograd(args):
 
 
 def run_reference(args):
+    """The reference arm: the oracle (there is no reference implementation; the reference is
+    the paper) on the headline workload and policy, each step one complete solve by the C
+    oracle on all host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    times = []
+    from oracle import c_oracle
+    c_oracle.build()
+    grid = args.grid or GRID
     for _ in range(args.warmup):
-        _oracle_sample(args.cpu_iters)
+        _c_oracle_solve(args.precision, grid)
     per = []
+    last = None
     for _ in range(args.steps):
-        s = _oracle_sample(args.cpu_iters)
-        per.append(s["seconds"] / s["iterations"])
-    iters = _golden_iterations(2000)
-    value = statistics.mean(per) * iters * 1e3
+        last = _c_oracle_solve(args.precision, grid)
+        per.append(last["seconds"] * 1e3)
+    value = statistics.mean(per)
+    pol = HEADLINE_POLICY[args.precision]
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms",
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(value, 1), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "convdiff2d_1024x1024_dia5_jacobi_tol1e-10", "precision": "fp64",
-                       "replacement": {"rr_period": 100}},
-            "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": "%d iterations per step of the numpy oracle, extrapolated to %d iterations"
-                                       % (args.cpu_iters, iters), "host": _host()},
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": "convdiff2d_%dx%d_dia5_jacobi_tol1e-10" % (grid, grid), "precision": args.precision,
+                       "policy": {k: v for k, v in pol.items() if k != "mixed"}},
+            "iterations": last["iterations"], "status": last["status"], "rel_res_true": last["rel_res_true"],
+            "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": c_oracle.threads(), "kind": "oracle",
+                             "sample": "%d complete solves by the C oracle (OpenMP, all host cores), %d iterations "
+                                       "each" % (args.steps, last["iterations"]), "host": _host()},
             "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -579,18 +662,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--theta", type=float, default=3e-3, help="mixed variant: relative replacement trigger")
-    ap.add_argument("--mixed-period", type=int, default=0, help="mixed variant: replacement period")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                    help="headline variant: mixed (FP32 recurrences with FP64 restarts) or fp64")
     ap.add_argument("--max-it", type=int, default=20000)
-    ap.add_argument("--cpu-iters", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", action="store_true", help="measure the headline variant only")
-    ap.add_argument("--grid", type=int, default=0, help="grid size per dimension (profiling of smaller cases)")
+    ap.add_argument("--grid", type=int, default=0, help="2D grid size per dimension (profiling of smaller cases)")
+    ap.add_argument("--grid3", type=int, default=0, help="3D grid size per dimension (profiling of smaller cases)")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D 256^3 workload")
     ap.add_argument("--workload", default="convdiff2d", choices=["convdiff2d", "convdiff3d", "batched", "autograd"],
-                    help="convdiff2d: 2D convection-diffusion 1024^2 DIA (default); convdiff3d: 3D 256^3 CSR "
-                         "Neumann-2; batched: 512 banded systems; autograd: differentiable solve, 16 RHS, "
-                         "forward + backward")
+                    help="convdiff2d (default): 2D convection-diffusion 1024^2 DIA headline, with the 3D 256^3 CSR "
+                         "Neumann-2 system measured alongside; convdiff3d: the 3D system alone; batched: 512 banded "
+                         "systems; autograd: differentiable solve, 16 RHS, forward + backward")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--clocks-csv", default=None, help="keep the raw nvidia-smi clock samples in this file")
     args = ap.parse_args()

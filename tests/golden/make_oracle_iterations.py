@@ -1,7 +1,7 @@
 """Write oracle_iterations_convdiff2d_1024.json: iterations the CPU oracle needs to reach
 a 1e-10 true relative residual on the 1024x1024 convection-diffusion system (Jacobi,
 FP64, periodic replacement every 100 iterations).  Calls only oracle/ and testproblems/.
-Used by bench.py to extrapolate its bounded CPU-oracle samples.  Takes a few minutes."""
+Used by the full-size GPU test of the replacement schedule.  Takes a few minutes."""
 import json
 import os
 import sys
