@@ -179,7 +179,8 @@ typedef struct pbcg_options {
                               holds no registers); 0 = automatic (1 for the one-row kernels
                               of a stencil system whose working set exceeds L2, else off),
                               < 0 = off, at most 16                                      */
-  int32_t barrier_overlap; /* single-system solver: > 0 = on where it applies, <= 0 = off.  Each block arrives at the grid barrier that ends a
+  int32_t barrier_overlap; /* single-system solver: 0 = automatic (on where it applies), < 0
+                              = off.  Each block arrives at the grid barrier that ends a
                               reduction phase, computes the next SPMV for the rows of its
                               chunk whose operands are all its own rows, then waits: the
                               on-chip form of overlapping a global reduction with the SPMV
@@ -267,6 +268,22 @@ pbcg_status pbicgstab_solve_multi(pbcg_ctx* ctx, int32_t nrhs, const double* B, 
  * modified.  Errors: INVALID_ARG (NULL, or src not CSR), OUT_OF_MEMORY,
  * CUDA_ERROR, or any error of pbicgstab_create for A^T (e.g. a zero diagonal). */
 pbcg_status pbicgstab_create_transpose(pbcg_ctx** out, const pbcg_ctx* src);
+
+/* Replace the values of the context's matrix, keeping its sparsity pattern (CSR: the
+ * row pointers and columns given at create; DIA: the offsets) and its options and
+ * workspace: everything derived from the values is rebuilt (validation, FP64 and FP32
+ * copies, D^{-1}, A D^{-1}, the stencil detection and the bound constants) -- what a
+ * differentiable solve needs when only the values change between calls.  val: device,
+ * nnz (CSR) or ndiag*n (DIA) values of val_dtype, read only.  Waits for the context's
+ * stream first.  Errors: INVALID_ARG (NULL, bad dtype, an invalid matrix: the context then
+ * refuses to solve until a later update succeeds), OUT_OF_MEMORY, CUDA_ERROR. */
+pbcg_status pbicgstab_update_values(pbcg_ctx* ctx, const void* val, int32_t val_dtype);
+
+/* Refresh a transposed context (made by pbicgstab_create_transpose from src) after src's
+ * values changed (pbicgstab_update_values on src): A^T's values are gathered from src's
+ * through the permutation kept at create_transpose.  Errors: INVALID_ARG (t not a
+ * transpose context, or src's pattern differs), OUT_OF_MEMORY, CUDA_ERROR. */
+pbcg_status pbicgstab_update_transpose(pbcg_ctx* t, const pbcg_ctx* src);
 
 /* Gradient of a loss with respect to the stored CSR values of the context's
  * matrix, given the adjoint solutions Lam (A^T Lam = dL/dX) and the solutions X

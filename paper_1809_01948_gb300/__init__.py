@@ -15,7 +15,7 @@ from . import _capi as capi
 from ._capi import Result, STATUS_NAMES  # noqa: F401
 
 __all__ = ["Solver", "BatchSolver", "PBCGError", "build", "STATUS_NAMES", "test_barrier_timeout",
-           "SparseSolve", "sparse_solve"]
+           "SparseSolve", "sparse_solve", "clear_solve_cache"]
 
 
 class PBCGError(RuntimeError):
@@ -214,6 +214,19 @@ class Solver:
         _check(_lib().pbicgstab_create_transpose(C.byref(t.ctx), self.ctx), "pbicgstab_create_transpose")
         return t
 
+    def update_values(self, val: torch.Tensor):
+        """New matrix values, same pattern (``pbicgstab_update_values``): CSR nnz values or
+        the DIA (ndiag, n) block, float64 or float32, on the device."""
+        if not (isinstance(val, torch.Tensor) and val.is_cuda and val.dtype in (torch.float64, torch.float32)):
+            raise ValueError("val must be a CUDA float64 or float32 tensor")
+        val = val.contiguous()
+        _check(_lib().pbicgstab_update_values(self.ctx, _ptr(val), capi.F64 if val.dtype == torch.float64 else capi.F32),
+               "pbicgstab_update_values")
+
+    def update_transpose(self, src: "Solver"):
+        """This context was made by ``src.transpose()``: take src's current values (``pbicgstab_update_transpose``)."""
+        _check(_lib().pbicgstab_update_transpose(self.ctx, src.ctx), "pbicgstab_update_transpose")
+
     def value_grad(self, Lam: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
         """-sum_c Lam[row_e, c] X[col_e, c] over the stored CSR entries (``pbicgstab_csr_value_grad``)."""
         if not (isinstance(X, torch.Tensor) and isinstance(Lam, torch.Tensor) and X.dim() == 2
@@ -361,6 +374,57 @@ class BatchSolver:
             pass
 
 
+class _ContextCache:
+    """Solver contexts of the differentiable solve, reused across calls with the same
+    sparsity pattern and options: a new call refreshes the values (``update_values``) and
+    the transposed context (``update_transpose``) instead of creating both again."""
+
+    def __init__(self, size: int = 4):
+        self.size = size
+        self.entries = {}   # key -> [solver, transpose or None, version of its values, version, row_ptr, col]
+
+    @staticmethod
+    def key(n, row_ptr, col, opts):
+        return (n, row_ptr.data_ptr(), row_ptr.numel(), col.data_ptr(), col.numel(), row_ptr.device.index,
+                tuple(sorted(opts.items())))
+
+    def forward_solver(self, n, values, row_ptr, col, opts):
+        k = self.key(n, row_ptr, col, opts)
+        e = self.entries.get(k)
+        if e is None:
+            if len(self.entries) >= self.size:
+                old = self.entries.pop(next(iter(self.entries)))
+                old[0].close()
+                if old[1] is not None:
+                    old[1].close()
+            s = Solver(n, row_ptr=row_ptr, col=col, val=values.detach(), **opts)
+            # the entry holds the pattern tensors, so their storage (the key) cannot be reused
+            e = self.entries[k] = [s, None, -1, 0, row_ptr, col]
+        else:
+            e[0].update_values(values.detach())
+            e[3] += 1
+        return e
+
+    @staticmethod
+    def transpose_solver(e):
+        if e[1] is None:
+            e[1] = e[0].transpose()
+        elif e[2] != e[3]:
+            e[1].update_transpose(e[0])
+        e[2] = e[3]
+        return e[1]
+
+    def clear(self):
+        for e in self.entries.values():
+            e[0].close()
+            if e[1] is not None:
+                e[1].close()
+        self.entries.clear()
+
+
+_CACHE = _ContextCache()
+
+
 class SparseSolve(torch.autograd.Function):
     """X = A^{-1} B with A given by CSR values (differentiable in ``values`` and ``B``).
 
@@ -368,37 +432,50 @@ class SparseSolve(torch.autograd.Function):
     backward: adjoint p-BiCGStab on A^T (``pbicgstab_create_transpose``) for the upstream
               gradient G = dL/dX: Lam = A^{-T} G; dL/dB = Lam; dL/dvalues = -sum_c Lam[row] X[col]
               (``pbicgstab_csr_value_grad``).
+    The contexts for A and A^T are kept per sparsity pattern and options and refreshed with
+    the new values on later calls (``pbicgstab_update_values`` / ``pbicgstab_update_transpose``).
+    A backward pass must run before the next forward with the same pattern (it reads the
+    shared contexts).
     """
 
     @staticmethod
     def forward(ctx, values, B, row_ptr, col, opts):
         n = B.shape[0]
-        s = Solver(n, row_ptr=row_ptr, col=col, val=values.detach(), **opts)
+        e = _CACHE.forward_solver(n, values, row_ptr, col, opts)
+        s = e[0]
         X, res = s.solve_multi(B.detach())
         bad = [r.status for r in res if r.status != capi.PBCG_OK]
         if bad:
             raise PBCGError(bad[0], "forward solve did not converge")
-        ctx.solver = s
+        ctx.entry = e
+        ctx.version = e[3]
         ctx.save_for_backward(X)
         return X
 
     @staticmethod
     def backward(ctx, G):
         (X,) = ctx.saved_tensors
-        s = ctx.solver
-        st = s.transpose()
+        e = ctx.entry
+        if e[3] != ctx.version:
+            raise RuntimeError("sparse_solve: another forward pass with the same pattern ran before this backward")
+        s = e[0]
+        st = _CACHE.transpose_solver(e)
         Lam, res = st.solve_multi(G.contiguous())
         bad = [r.status for r in res if r.status != capi.PBCG_OK]
         if bad:
             raise PBCGError(bad[0], "adjoint solve did not converge")
         gvals = s.value_grad(Lam, X) if ctx.needs_input_grad[0] else None
-        st.close()
         return gvals, (Lam if ctx.needs_input_grad[1] else None), None, None, None
 
 
 def sparse_solve(values, B, row_ptr, col, **opts):
     """Differentiable solve X = A^{-1} B (A in CSR with the given values)."""
     return SparseSolve.apply(values, B, row_ptr, col, opts)
+
+
+def clear_solve_cache():
+    """Release the contexts ``sparse_solve`` keeps between calls."""
+    _CACHE.clear()
 
 
 def propagation_norms(hist: torch.Tensor, iters: int, stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:

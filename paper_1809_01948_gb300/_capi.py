@@ -82,6 +82,8 @@ PROTOTYPES = {
     "pbicgstab_true_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "pbicgstab_get_vector": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "pbicgstab_launch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "pbicgstab_update_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "pbicgstab_update_transpose": (C.c_int, [C.c_void_p, C.c_void_p]),
     "pbicgstab_destroy": (C.c_int, [C.c_void_p]),
     "pbicgstab_last_error": (C.c_char_p, []),
     "pbicgstab_test_barrier_timeout": (C.c_int, [C.c_double, C.c_int32, C.POINTER(C.c_int32)]),

@@ -288,7 +288,7 @@ static void free_ctx(pbcg_ctx* c) {
   if (c->valAu && c->valAu != (void*)c->val64) cudaFree(c->valAu);
   void* ptrs[] = {c->row_ptr, c->col, c->val64, c->valAt, c->diag64, c->dinv64, c->dinvT, c->st_mask,
                   c->vecs, c->part, c->dstate, c->multi_vecs, c->multi_part, c->multi_state, c->multi_params,
-                  c->xbest};
+                  c->xbest, c->tperm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->hstate) cudaFreeHost(c->hstate);
@@ -422,7 +422,9 @@ extern "C" pbcg_status pbicgstab_default_options(pbcg_options* o) {
 
 extern "C" const char* pbicgstab_last_error(void) { return g_last_error.c_str(); }
 
-static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
+// copy_pattern: copy A's CSR row pointers and columns (create); false: A's pattern is the
+// context's own (pbicgstab_update_values), only the values are new.
+static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A, bool copy_pattern = true) {
   const int n = c->n;
   const int nb = (n + 255) / 256;
   const int f32 = A->val_dtype == PBCG_F32;
@@ -433,11 +435,14 @@ static pbcg_status prepare_matrix(pbcg_ctx* c, const pbcg_matrix* A) {
   long long nval;
   if (c->fmt == PBCG_FMT_CSR) {
     nval = c->nnz;
-    CK(cudaMalloc(&c->row_ptr, sizeof(int) * (n + 1)), "cudaMalloc row_ptr");
-    CK(cudaMalloc(&c->col, sizeof(int) * std::max<long long>(1, c->nnz)), "cudaMalloc col");
-    CK(cudaMemcpyAsync(c->row_ptr, A->row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, c->stream), "copy row_ptr");
-    if (c->nnz)
-      CK(cudaMemcpyAsync(c->col, A->col, sizeof(int) * c->nnz, cudaMemcpyDeviceToDevice, c->stream), "copy col");
+    if (copy_pattern) {
+      CK(cudaMalloc(&c->row_ptr, sizeof(int) * (n + 1)), "cudaMalloc row_ptr");
+      CK(cudaMalloc(&c->col, sizeof(int) * std::max<long long>(1, c->nnz)), "cudaMalloc col");
+      CK(cudaMemcpyAsync(c->row_ptr, A->row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, c->stream),
+         "copy row_ptr");
+      if (c->nnz)
+        CK(cudaMemcpyAsync(c->col, A->col, sizeof(int) * c->nnz, cudaMemcpyDeviceToDevice, c->stream), "copy col");
+    }
     CK(cudaMemsetAsync(&c->dstate->reserved, 0, 2 * sizeof(int), c->stream), "memset");
     validate_csr_kernel<<<nb, 256, 0, c->stream>>>(n, c->nnz, c->row_ptr, c->col, A->val, f32, need_diag, dflags, c->diag64,
                                                     &c->dstate->reserved, &c->dstate->maxnnz);
@@ -624,6 +629,40 @@ extern "C" pbcg_status pbicgstab_create(pbcg_ctx** out, const pbcg_matrix* A, co
 #undef CKC
 }
 
+// Release what depends on the matrix values (kept: the pattern, the workspace, the state).
+static void free_values(pbcg_ctx* c) {
+  if (c->valAu && c->valAu != (void*)c->val64) cudaFree(c->valAu);
+  void* ptrs[] = {c->val64, c->valAt, c->diag64, c->dinv64, c->dinvT, c->st_mask};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  c->val64 = nullptr; c->valAt = nullptr; c->valAu = nullptr; c->diag64 = nullptr; c->dinv64 = nullptr;
+  c->dinvT = nullptr; c->st_mask = nullptr;
+  c->stencil = 0; c->st_n = 0; c->st_dinv = 0.0; c->dconst = 0; c->dconst_inv = 0.0;
+  c->bandwidth = 0; c->maxnnz = 0; c->ndiag_t = 0; c->at_unit_diag = 0; c->norm_bound = 0.0; c->dinv_max = 1.0;
+}
+
+extern "C" pbcg_status pbicgstab_update_values(pbcg_ctx* c, const void* val, int32_t val_dtype) {
+  if (!c || !val) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_update_values");
+  if (val_dtype != PBCG_F64 && val_dtype != PBCG_F32) return set_error(PBCG_INVALID_ARG, "unknown value dtype");
+  CK(cudaStreamSynchronize(c->stream), "pending work");   // no solve may still read the old values
+  pbcg_matrix A;
+  memset(&A, 0, sizeof A);
+  A.format = c->fmt;
+  A.val_dtype = val_dtype;
+  A.n = c->n;
+  A.nnz = c->nnz;
+  A.row_ptr = c->row_ptr;
+  A.col = c->col;
+  A.val = val;
+  A.ndiag = c->ndiag;
+  A.offsets = c->offsets;
+  free_values(c);
+  const pbcg_status st = prepare_matrix(c, &A, false);
+  if (st != PBCG_OK) c->valid = 0;
+  else c->valid = 1;
+  return st;
+}
+
 extern "C" pbcg_status pbicgstab_set_options(pbcg_ctx* c, const pbcg_options* opt) {
   if (!c || !opt) return set_error(PBCG_INVALID_ARG, "NULL argument");
   pbcg_status st = check_options(opt, c->n);
@@ -654,6 +693,7 @@ pbcg_status enqueue_true_residual(pbcg_ctx* c, const double* b, const double* x,
 }
 
 static pbcg_status enqueue_solve(pbcg_ctx* c, const double* b, double* x) {
+  if (!c->valid) return set_error(PBCG_INVALID_ARG, "the context's last pbicgstab_update_values failed");
   int grid = 0, threads = 0;
   const bool vec = quad_rows(c, b, x);
   pbcg_status st = launch_shape(c, &grid, &threads, vec);

@@ -93,6 +93,8 @@ struct pbcg_ctx {
   DevState* hstate = nullptr;  // pinned
   double* xbest = nullptr;     // best (re)start iterate of options.stag_window (n doubles)
   int launch[4] = {0, 0, 0, 0};  // last solve: grid, threads, rows per thread, prefetch distance
+  int valid = 1;               // 0 after a failed pbicgstab_update_values: solves are refused
+  int* tperm = nullptr;        // transpose contexts: entry e of A^T is entry tperm[e] of the source
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // multi-RHS workspace (grown on demand by pbicgstab_solve_multi)
   int multi_cap = 0;           // right-hand sides the buffers below hold
@@ -243,7 +245,7 @@ inline SolverParams<T> make_params(pbcg_ctx* c, const double* b, double* x, int 
   p.rr_cutoff = c->opt.rr_cutoff > 0.0 ? c->opt.rr_cutoff : 1.4901161193847656e-08;   // sqrt(2^-52)
   p.strided = c->bandwidth > p.chunk / 2 ? 1 : 0;
   p.halo = c->bandwidth;
-  p.overlap = (c->opt.barrier_overlap > 0 && !p.strided && c->prec_kind != PBCG_PREC_NEUMANN &&
+  p.overlap = (c->opt.barrier_overlap >= 0 && !p.strided && c->prec_kind != PBCG_PREC_NEUMANN &&
                c->opt.method == PBCG_PIPELINED && !c->opt.rr_auto && grid > 1 && p.chunk > 2 * c->bandwidth) ? 1 : 0;
   // stencil storage only: with CSR / DIA values the row products already keep several
   // loads per row in flight (measured slower with the prefetch on the 3D CSR operator)

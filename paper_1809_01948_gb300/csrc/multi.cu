@@ -44,7 +44,7 @@ __global__ void scan_kernel(int n, const int* cnt, int* out) {
 }
 
 __global__ void scatter_kernel(int n, const int* row_ptr, const int* col, const double* val, const int* rpT,
-                               int* fill, int* colT, double* valT) {
+                               int* fill, int* colT, double* valT, int* perm) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
@@ -52,23 +52,33 @@ __global__ void scatter_kernel(int n, const int* row_ptr, const int* col, const 
     const int pos = rpT[j] + atomicAdd(fill + j, 1);
     colT[pos] = i;
     valT[pos] = val[e];
+    perm[pos] = e;
   }
 }
 
 // Insertion sort of each transposed row by column: makes the result independent of
 // the atomic order above (rows of A^T are short for the stencil-type matrices here).
-__global__ void sort_rows_kernel(int n, const int* rp, int* col, double* val) {
+// perm follows the entries, so valT[k] = val[perm[k]] afterwards.
+__global__ void sort_rows_kernel(int n, const int* rp, int* col, double* val, int* perm) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int e0 = rp[i], e1 = rp[i + 1];
   for (int e = e0 + 1; e < e1; ++e) {
     const int c = col[e];
     const double v = val[e];
+    const int pe = perm[e];
     int f = e - 1;
-    while (f >= e0 && col[f] > c) { col[f + 1] = col[f]; val[f + 1] = val[f]; --f; }
+    while (f >= e0 && col[f] > c) { col[f + 1] = col[f]; val[f + 1] = val[f]; perm[f + 1] = perm[f]; --f; }
     col[f + 1] = c;
     val[f + 1] = v;
+    perm[f + 1] = pe;
   }
+}
+
+// dst[k] = src[perm[k]]
+__global__ void gather_kernel(long long m, const int* perm, const double* src, double* dst) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k < m) dst[k] = src[perm[k]];
 }
 
 // ---------------------------------------------------------------- value gradient
@@ -218,7 +228,7 @@ extern "C" pbcg_status pbicgstab_create_transpose(pbcg_ctx** out, const pbcg_ctx
   const int n = src->n;
   const long long nnz = src->nnz;
   cudaStream_t s = src->stream;
-  int *cnt = nullptr, *rpT = nullptr, *colT = nullptr;
+  int *cnt = nullptr, *rpT = nullptr, *colT = nullptr, *perm = nullptr;
   double* valT = nullptr;
   pbcg_status st = PBCG_OK;
   auto fail = [&](pbcg_status e) {
@@ -226,19 +236,21 @@ extern "C" pbcg_status pbicgstab_create_transpose(pbcg_ctx** out, const pbcg_ctx
     if (rpT) cudaFree(rpT);
     if (colT) cudaFree(colT);
     if (valT) cudaFree(valT);
+    if (perm) cudaFree(perm);
     return e;
   };
   if ((st = cuda_status(cudaMalloc(&cnt, sizeof(int) * (n + 1)), "cudaMalloc")) != PBCG_OK) return fail(st);
   if ((st = cuda_status(cudaMalloc(&rpT, sizeof(int) * (n + 1)), "cudaMalloc")) != PBCG_OK) return fail(st);
   if ((st = cuda_status(cudaMalloc(&colT, sizeof(int) * std::max<long long>(1, nnz)), "cudaMalloc")) != PBCG_OK) return fail(st);
   if ((st = cuda_status(cudaMalloc(&valT, sizeof(double) * std::max<long long>(1, nnz)), "cudaMalloc")) != PBCG_OK) return fail(st);
+  if ((st = cuda_status(cudaMalloc(&perm, sizeof(int) * std::max<long long>(1, nnz)), "cudaMalloc")) != PBCG_OK) return fail(st);
   cudaMemsetAsync(cnt, 0, sizeof(int) * (n + 1), s);
   const unsigned nbe = (unsigned)((nnz + 255) / 256), nbr = (unsigned)((n + 255) / 256);
   if (nnz) count_cols_kernel<<<nbe, 256, 0, s>>>(nnz, src->col, cnt);
   scan_kernel<<<1, 1024, 0, s>>>(n, cnt, rpT);
   cudaMemsetAsync(cnt, 0, sizeof(int) * (n + 1), s);
-  scatter_kernel<<<nbr, 256, 0, s>>>(n, src->row_ptr, src->col, src->val64, rpT, cnt, colT, valT);
-  sort_rows_kernel<<<nbr, 256, 0, s>>>(n, rpT, colT, valT);
+  scatter_kernel<<<nbr, 256, 0, s>>>(n, src->row_ptr, src->col, src->val64, rpT, cnt, colT, valT, perm);
+  sort_rows_kernel<<<nbr, 256, 0, s>>>(n, rpT, colT, valT, perm);
   if ((st = cuda_status(cudaGetLastError(), "transpose kernels")) != PBCG_OK) return fail(st);
   pbcg_matrix m;
   memset(&m, 0, sizeof m);
@@ -253,7 +265,27 @@ extern "C" pbcg_status pbicgstab_create_transpose(pbcg_ctx** out, const pbcg_ctx
   M.kind = src->prec_kind;
   M.degree = src->degree;
   st = pbicgstab_create(out, &m, &M, &src->opt, (void*)s);
+  if (st == PBCG_OK) {   // the permutation stays with the transpose context (value updates)
+    (*out)->tperm = perm;
+    perm = nullptr;
+  }
   return fail(st);   // the new context holds its own copies
+}
+
+extern "C" pbcg_status pbicgstab_update_transpose(pbcg_ctx* t, const pbcg_ctx* src) {
+  if (!t || !src) return set_error(PBCG_INVALID_ARG, "NULL argument to pbicgstab_update_transpose");
+  if (!t->tperm || t->n != src->n || t->nnz != src->nnz || src->fmt != PBCG_FMT_CSR)
+    return set_error(PBCG_INVALID_ARG, "pbicgstab_update_transpose needs a context made by pbicgstab_create_transpose "
+                                       "from a matrix with the source's pattern");
+  double* valT = nullptr;
+  MCK(cudaMalloc(&valT, sizeof(double) * std::max<long long>(1, t->nnz)), "cudaMalloc");
+  const long long m = t->nnz;
+  if (m) gather_kernel<<<(unsigned)((m + 255) / 256), 256, 0, src->stream>>>(m, t->tperm, src->val64, valT);
+  pbcg_status st = cuda_status(cudaGetLastError(), "gather kernel");
+  if (st == PBCG_OK) st = cuda_status(cudaStreamSynchronize(src->stream), "gather");
+  if (st == PBCG_OK) st = pbicgstab_update_values(t, valT, PBCG_F64);
+  cudaFree(valT);
+  return st;
 }
 
 extern "C" pbcg_status pbicgstab_csr_value_grad(pbcg_ctx* c, int32_t nrhs, const double* Lam, const double* X,

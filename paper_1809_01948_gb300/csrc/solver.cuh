@@ -1067,10 +1067,18 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
 // by memory-level parallelism, so STREAM trades registers (40, with some spilling) for 48
 // resident warps per SM (three 512-thread blocks): 1173 vs 1301 us per iteration on the
 // 256^3 Neumann system (FP64 at that budget loses 12%).
+// The four-row (VEC) kernels: 512-thread blocks, one per SM (128 registers, no spills); the
+// build parameters below let a build trade registers for resident warps.
+#ifndef PBCG_VEC_THREADS
+#define PBCG_VEC_THREADS 512
+#endif
+#ifndef PBCG_VEC_BLOCKS_PER_SM
+#define PBCG_VEC_BLOCKS_PER_SM 1
+#endif
 template <typename T, bool STREAM, bool VEC = false>
 struct SolverLaunch {
-  static constexpr int kThreads = VEC ? 512 : STREAM ? 512 : kMaxThreads;
-  static constexpr int kBlocksPerSM = VEC ? 1 : STREAM ? 3 : 1;
+  static constexpr int kThreads = VEC ? PBCG_VEC_THREADS : STREAM ? 512 : kMaxThreads;
+  static constexpr int kBlocksPerSM = VEC ? PBCG_VEC_BLOCKS_PER_SM : STREAM ? 3 : 1;
 };
 
 // One cooperative grid solves one system.  AUTO adds the automated replacement policy

@@ -220,3 +220,33 @@ def test_autograd_full_size_convdiff2d_512_16rhs():
     for pairs in (fb, fv):
         fd, g = pairs[:, 0], pairs[:, 1]
         assert np.all(np.abs(fd - g) <= 1e-5 * np.abs(g) + 1e-6 * np.abs(g).max()), np.abs(fd - g) / np.abs(g)
+
+
+def test_autograd_reuses_its_contexts_across_value_updates():
+    """Three calls with one sparsity pattern and changing values: the first creates the A and
+    A^T contexts, the later ones refresh their values (pbicgstab_update_values /
+    pbicgstab_update_transpose); every call's gradients match the dense adjoint of its own
+    values (a stale value anywhere would show)."""
+    import dataclasses
+    torch = torch_cuda()
+    import paper_1809_01948_gb300 as pb
+    m = tp.problem_convdiff2d_multi(n=32, nrhs=16)
+    rp, col, val = _csr_tensors(torch, m.A)
+    rng = np.random.Generator(np.random.PCG64(21))
+    pb.clear_solve_cache()
+    Xt = torch.from_numpy(m.X_target).cuda()
+    for call in range(3):
+        scale = 1.0 + (0.0 if call == 0 else 0.05) * rng.uniform(-1.0, 1.0, m.A.nnz)
+        vnp = m.A.val * scale
+        values = torch.from_numpy(vnp).cuda().requires_grad_(True)
+        B = torch.from_numpy(m.B).cuda().requires_grad_(True)
+        X = pb.sparse_solve(values, B, rp, col, precond="jacobi", tol=1e-13, max_it=30000, rr_period=100,
+                            rr_theta=1e-3, max_restarts=3)
+        ((X - Xt) ** 2).sum().backward()
+        Ac = dataclasses.replace(m.A, val=vnp)
+        Xd, gBd, gvd = adjoint.dense_adjoint(Ac, m.B, m.X_target)
+        assert np.linalg.norm(X.detach().cpu().numpy() - Xd) <= 1e-10 * np.linalg.norm(Xd), call
+        assert np.linalg.norm(B.grad.cpu().numpy() - gBd) <= 1e-6 * np.linalg.norm(gBd), call
+        assert np.linalg.norm(values.grad.cpu().numpy() - gvd) <= 1e-6 * np.linalg.norm(gvd), call
+    assert len(pb._CACHE.entries) == 1
+    pb.clear_solve_cache()

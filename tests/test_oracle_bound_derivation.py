@@ -288,3 +288,24 @@ def test_gap_bound_initial_values_follow_the_model():
         want = _evaluate(product("A", leaf("v"))[1], dict(v=float(np.linalg.norm(vec)), nA=c["nA"],
                                                           msn=c["mu"] * c["sqrtN"])) * EPS
         assert abs(getattr(gb, attr) - want) <= 1e-14 * want, attr
+
+
+def test_bound_constants_closed_forms():
+    """mu, mu~, sqrt(N) and the norm bounds on a hand-sized matrix: row 1 has 3 entries;
+    column sums of |A| are 6, 9, 7 and row sums 5, 8, 9, so sqrt(||A||_1 ||A||_inf) = 9;
+    Jacobi's ||M^{-1}|| bound is max |1/a_ii| = 1/4 with one entry per row; the degree-1
+    Neumann polynomial D^{-1} + (I - D^{-1}A) D^{-1}, formed densely here, has A's
+    tridiagonal pattern (3 entries in its middle row)."""
+    import scipy.sparse as sp
+    a = np.array([[4.0, -1.0, 0.0], [-2.0, 5.0, -1.0], [0.0, -3.0, 6.0]])
+    A = sp.csr_matrix(a)
+    c = diagnostics.bound_constants(A, make_precond("jacobi", A, 0, np.float64))
+    assert c["mu"] == 3 and c["mut"] == 1 and abs(c["sqrtN"] - math.sqrt(3)) < 1e-15
+    assert abs(c["nA"] - 9.0) < 1e-14 and abs(c["nM"] - 0.25) < 1e-15
+    assert np.linalg.svd(a, compute_uv=False)[0] <= c["nA"]
+    D = np.diag(1.0 / np.diag(a))
+    P = D + (np.eye(3) - D @ a) @ D
+    cn = diagnostics.bound_constants(A, make_precond("neumann", A, 1, np.float64))
+    assert cn["mut"] == max(int(np.count_nonzero(np.abs(row) > 0)) for row in P) == 3
+    ap = np.abs(P)
+    assert abs(cn["nM"] - math.sqrt(ap.sum(axis=0).max() * ap.sum(axis=1).max())) < 1e-14
