@@ -137,7 +137,9 @@ typedef struct pbcg_options {
                               storage whose row count is a multiple of 4, solved with
                               16-byte aligned b and x (and hist_x) by Algorithm 2 without
                               rr_auto, runs kernels that take four rows per thread in the
-                              hot passes when block_threads is 0 (then 512) or <= 512   */
+                              hot passes when block_threads is 0 or at most their block
+                              size: 512, or 768 for a mixed solve whose working set
+                              exceeds L2 (0 selects that size)                           */
   int32_t max_restarts;    /* after a breakdown (zero or non-finite omega, (r0,r_i),
                               beta or alpha denominator) restart Algorithm 2 from the
                               current iterate with a new shadow vector, at most this many
@@ -187,6 +189,14 @@ typedef struct pbcg_options {
                               (Section 1).  Applies with the chunked row order (matrix
                               bandwidth below half a chunk), no or Jacobi preconditioning,
                               Algorithm 2 without rr_auto                               */
+  int32_t staged_sweeps;   /* single-system mixed solve with the four-row kernels and a
+                              Neumann preconditioner on stencil storage: > 0 stages the
+                              operands of the preconditioner's Jacobi sweeps in shared
+                              memory through a three-stage asynchronous-copy pipeline
+                              (same products in the same order as the register form);
+                              0 = off.  Ignored where it does not apply (offsets beyond
+                              4 x block_threads rows must be multiples of 4, and three
+                              stages must fit the block's shared memory)               */
 } pbcg_options;
 
 typedef struct pbcg_result {
@@ -316,7 +326,8 @@ pbcg_status pbicgstab_get_vector(pbcg_ctx* ctx, int32_t which, double* dst);
 /* The launch of the context's last single-system solve: info[0] grid blocks, info[1]
  * threads per block, info[2] rows per thread in the hot passes (1, or 4 for the four-row
  * kernels of the stencil storage), info[3] the L2 prefetch distance in row sweeps (0 =
- * off) plus 256 when the barriers overlap the interior SPMV rows (options.barrier_overlap).
+ * off) plus 256 when the barriers overlap the interior SPMV rows (options.barrier_overlap)
+ * plus 512 when the Neumann sweeps are staged in shared memory (options.staged_sweeps).
  * All zero before the first solve.  ctx, info: host, non-NULL.  Errors:
  * INVALID_ARG (NULL). */
 pbcg_status pbicgstab_launch_info(const pbcg_ctx* ctx, int32_t info[4]);

@@ -78,7 +78,8 @@ class Solver:
                  block_threads: int = 0, max_restarts: int = 0, rr_auto: bool = False, rr_tau: float = 0.0,
                  method: str = "pipelined", operator_storage: str = "auto", restart_period: int = 0,
                  stag_window: int = 0, rr_cutoff: float = 0.0, prefetch_trips: int = 0,
-                 barrier_overlap: int = 0, stream: Optional[torch.cuda.Stream] = None):
+                 barrier_overlap: int = 0, staged_sweeps: int = 0,
+                 stream: Optional[torch.cuda.Stream] = None):
         lib = _lib()
         self.n = int(n)
         self.stream = stream
@@ -131,6 +132,7 @@ class Solver:
         self.opt.rr_cutoff = rr_cutoff
         self.opt.prefetch_trips = prefetch_trips
         self.opt.barrier_overlap = barrier_overlap
+        self.opt.staged_sweeps = staged_sweeps
         self.ctx = C.c_void_p()
         _check(lib.pbicgstab_create(C.byref(self.ctx), C.byref(m), C.byref(p), C.byref(self.opt),
                                     _stream_handle(stream)), "pbicgstab_create")
@@ -257,7 +259,8 @@ class Solver:
         info = (C.c_int32 * 4)()
         _check(_lib().pbicgstab_launch_info(self.ctx, info), "pbicgstab_launch_info")
         return dict(grid_blocks=info[0], block_threads=info[1], rows_per_thread=info[2],
-                    prefetch_trips=info[3] % 256, barrier_overlap=info[3] // 256)
+                    prefetch_trips=info[3] % 256, barrier_overlap=(info[3] // 256) % 2,
+                    staged_sweeps=info[3] // 512)
 
     def get_vector(self, name: str) -> torch.Tensor:
         """A work vector of the last solve (``pbicgstab_get_vector``) as a CUDA float64 tensor."""

@@ -43,7 +43,8 @@ class Options(C.Structure):
                 ("operator_storage", C.c_int32), ("cluster_blocks", C.c_int32),
                 ("lanes_per_row", C.c_int32), ("batch_build", C.c_int32),
                 ("restart_period", C.c_int32), ("stag_window", C.c_int32), ("rr_cutoff", C.c_double),
-                ("prefetch_trips", C.c_int32), ("barrier_overlap", C.c_int32)]
+                ("prefetch_trips", C.c_int32), ("barrier_overlap", C.c_int32),
+                ("staged_sweeps", C.c_int32)]
 
 
 class Result(C.Structure):

@@ -105,6 +105,7 @@ __device__ void build_params(const BatchDev& d, int k, SolverParams<T, VR>& p) {
   p.strided = 0;
   p.overlap = 0;   // block and cluster teams: no grid barrier to overlap
   p.halo = 0;
+  p.staged = 0;
 }
 
 template <typename T, typename VR>

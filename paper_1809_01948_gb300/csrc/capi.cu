@@ -325,6 +325,7 @@ pbcg_status check_options(const pbcg_options* o, long long n) {
   if (!(o->rr_cutoff >= 0.0 && o->rr_cutoff < 1.0))
     return set_error(PBCG_INVALID_ARG, "options.rr_cutoff must be in [0, 1)");
   if (o->prefetch_trips > 16) return set_error(PBCG_INVALID_ARG, "options.prefetch_trips must be at most 16");
+  if (o->staged_sweeps < 0) return set_error(PBCG_INVALID_ARG, "options.staged_sweeps must be >= 0");
   if (o->method == PBCG_CLASSIC) {
     if (o->precision != PBCG_FP64) return set_error(PBCG_INVALID_ARG, "PBCG_CLASSIC runs in PBCG_FP64 only");
     if (o->rr_period != 0 || o->rr_theta != 0.0 || o->rr_auto != 0 || o->max_restarts != 0 ||
@@ -359,7 +360,8 @@ bool quad_rows(const pbcg_ctx* c, const double* b, const double* x) {
   const auto al = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
   return c->stencil && c->n % 4 == 0 && !c->opt.rr_auto && c->opt.method == PBCG_PIPELINED && al(b) && al(x) &&
          (c->opt.record_iterates == 0 || al(c->opt.hist_x)) &&
-         c->opt.block_threads <= pbcg::SolverLaunch<double, false, true>::kThreads;
+         c->opt.block_threads <= (streaming(c) ? pbcg::SolverLaunch<float, true, true>::kThreads
+                                               : pbcg::SolverLaunch<double, false, true>::kThreads);
 }
 
 template <typename T>
@@ -370,7 +372,7 @@ static const void* kernel_ptr(const pbcg_ctx* c, bool vec) {
     if (o.method == PBCG_CLASSIC) return classic_kernel_f64(sc);
     return pipelined_kernel_f64(o.rr_auto != 0, sc, vec);
   } else {
-    return pipelined_kernel_f32(o.rr_auto != 0, !vec && streaming(c), sc, vec);
+    return pipelined_kernel_f32(o.rr_auto != 0, streaming(c), sc, vec);
   }
 }
 
@@ -380,8 +382,30 @@ static const void* kernel_ptr(const pbcg_ctx* c, bool vec) {
 // SM for the streaming mixed build, two 512-thread blocks for the four-row kernels.
 static int kernel_threads(const pbcg_ctx* c, bool vec) {
   if (c->opt.block_threads) return c->opt.block_threads;
-  if (vec) return pbcg::SolverLaunch<double, false, true>::kThreads;
+  if (vec)
+    return streaming(c) ? pbcg::SolverLaunch<float, true, true>::kThreads : pbcg::SolverLaunch<double, false, true>::kThreads;
   return streaming(c) ? pbcg::SolverLaunch<float, true>::kThreads : pbcg::SolverLaunch<double, false>::kThreads;
+}
+
+// Dynamic shared memory of the staged Neumann sweeps (options.staged_sweeps): three stages
+// of the layout stage_layout gives for a block's 4 x threads rows; 0 where they do not
+// apply (another kernel build, an offset the layout cannot stage, or no room beside the
+// kernel's static shared memory).
+size_t staged_bytes(const pbcg_ctx* c, int threads, bool vec) {
+  if (c->opt.staged_sweeps <= 0 || !vec || c->precision != PBCG_MIXED || c->prec_kind != PBCG_PREC_NEUMANN ||
+      !c->stencil)
+    return 0;
+  const pbcg::MatView<float> v = make_stencil_view<float>(c, false);
+  const pbcg::StageLayout L = pbcg::stage_layout(v.off, v.ndiag, 4 * threads);
+  if (!L.ok) return 0;
+  const size_t bytes = (size_t)3 * (size_t)L.stage_f * sizeof(float);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel_ptr<float>(c, vec)) != cudaSuccess) return 0;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return fa.sharedSizeBytes + bytes <= (size_t)optin ? bytes : 0;
 }
 
 pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads, bool vec) {
@@ -392,7 +416,10 @@ pbcg_status launch_shape(const pbcg_ctx* c, int* grid, int* threads, bool vec) {
   CK(cudaFuncGetAttributes(&fa, k), "kernel attributes");
   if (nt > fa.maxThreadsPerBlock)
     return set_error(PBCG_INVALID_ARG, "block_threads %d above this solver's limit of %d", nt, fa.maxThreadsPerBlock);
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, 0), "occupancy query");
+  const size_t dyn = staged_bytes(c, nt, vec);
+  if (dyn > 0)
+    CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn), "shared memory attribute");
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, dyn), "occupancy query");
   const int sms = sm_count();
   const int max_coresident = per_sm * sms;
   if (max_coresident <= 0) return set_error(PBCG_INVALID_ARG, "kernel cannot be resident with %d threads per block", nt);
@@ -705,9 +732,13 @@ static pbcg_status enqueue_solve(pbcg_ctx* c, const double* b, double* x) {
   CK(cudaEventRecord(c->ev0, c->stream), "event record");
   if (c->precision == PBCG_MIXED) {
     SolverParams<float> p = make_params<float>(c, b, x, grid, vec);
-    c->launch[0] = grid; c->launch[1] = threads; c->launch[2] = vec ? 4 : 1; c->launch[3] = p.prefetch + 256 * p.overlap;
+    const size_t dyn = staged_bytes(c, threads, vec);
+    p.staged = dyn > 0 ? 1 : 0;
+    c->launch[0] = grid; c->launch[1] = threads; c->launch[2] = vec ? 4 : 1;
+    c->launch[3] = p.prefetch + 256 * p.overlap + 512 * p.staged;
     void* args[] = {&p};
-    CK(cudaLaunchCooperativeKernel(kernel_ptr<float>(c, vec), grid, threads, args, 0, c->stream), "cooperative launch");
+    CK(cudaLaunchCooperativeKernel(kernel_ptr<float>(c, vec), grid, threads, args, dyn, c->stream),
+       "cooperative launch");
   } else {
     SolverParams<double> p = make_params<double>(c, b, x, grid, vec);
     c->launch[0] = grid; c->launch[1] = threads; c->launch[2] = vec ? 4 : 1; c->launch[3] = p.prefetch + 256 * p.overlap;

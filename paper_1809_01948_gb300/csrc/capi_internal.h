@@ -18,7 +18,7 @@ const void* pipelined_kernel_f64(bool automated, bool scalar, bool vec);
 const void* pipelined_kernel_f32(bool automated, bool stream, bool scalar, bool vec);
 const void* classic_kernel_f64(bool scalar);
 const void* pipelined_kernel_f64_vec(bool scalar);
-const void* pipelined_kernel_f32_vec(bool scalar);
+const void* pipelined_kernel_f32_vec(bool scalar, bool stream);
 pbcg_status set_error(pbcg_status st, const char* fmt, ...);
 pbcg_status cuda_status(cudaError_t e, const char* what);
 int sm_count();

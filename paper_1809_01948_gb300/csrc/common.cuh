@@ -183,6 +183,58 @@ __device__ __forceinline__ Quad<Acc> quad_dot(const MatView<V>& A, const X* __re
   return acc;
 }
 
+// ---------------------------------------------------------------- asynchronous copies
+// cp.async (global -> shared, no registers held while the copy is in flight), committed in
+// groups; cp.async.wait_group N returns once at most N of this thread's groups are pending.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared-memory layout of one stage of the staged stencil sweeps (four rows per thread, R =
+// 4 x threads rows per trip), the same on the host (dynamic shared memory size) and the
+// device: a near window of the gathered vector, rows [base - H, base + R + H) with H the
+// largest offset of magnitude <= R rounded up to 4 (at least 4); one R-row window per
+// farther offset (at base + offset, which must be a multiple of 4); the R own rows of the
+// source vector; the R row masks.  Sizes in floats; a stage is a multiple of 16 bytes.
+struct StageLayout {
+  int R, H, nfar;
+  int far[kMaxDiag];
+  int src_f, mask_f, stage_f;   // offsets of the parts within a stage, and its size
+  int ok;                       // 0: an offset this layout cannot stage
+};
+
+__host__ __device__ inline StageLayout stage_layout(const int* off, int ndiag, int R) {
+  StageLayout L;
+  L.R = R;
+  L.H = 0;
+  L.nfar = 0;
+  L.ok = 1;
+  for (int d = 0; d < ndiag; ++d) {
+    const int a = off[d] < 0 ? -off[d] : off[d];
+    if (a <= R) {
+      L.H = a > L.H ? a : L.H;
+    } else {
+      if (off[d] % 4 != 0) L.ok = 0;
+      L.far[L.nfar++] = off[d];
+    }
+  }
+  L.H = (L.H + 3) / 4 * 4;
+  if (L.H < 4) L.H = 4;   // the sweep reads up to 3 rows beyond a warp's first and last quad
+  L.src_f = (R + 2 * L.H) + L.nfar * R;
+  L.mask_f = L.src_f + R;
+  L.stage_f = L.mask_f + R / 2;          // R 16-bit masks
+  L.stage_f = (L.stage_f + 3) / 4 * 4;
+  return L;
+}
+
 // Hint: bring the 128-byte line holding *ptr into L2 (no register is written, so a
 // thread can request the next row's operands while it computes the current one).
 template <typename V>

@@ -5,7 +5,7 @@
 namespace pbcg {
 
 const void* pipelined_kernel_f32(bool automated, bool stream, bool scalar, bool vec) {
-  if (vec) return pipelined_kernel_f32_vec(scalar);
+  if (vec) return pipelined_kernel_f32_vec(scalar, stream);
   if (automated) return (const void*)pbicgstab_kernel<float, true>;
   if (stream)
     return scalar ? (const void*)pbicgstab_kernel<float, false, true, true> : (const void*)pbicgstab_kernel<float, false, true>;

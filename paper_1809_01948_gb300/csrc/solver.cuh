@@ -70,6 +70,8 @@ struct SolverParams {
   int max_restarts;     // restarts from the current iterate allowed after a breakdown
   int strided;          // grid team row order: 1 grid-stride, 0 one contiguous chunk per block
   int prefetch;         // > 0: request the operands of the row sweep this many trips ahead into L2
+  int staged;           // > 0: the four-row FP32 Neumann sweeps stage their operands in dynamic
+                        // shared memory (the kernel's launch provides three stages)
   int overlap;          // 1: compute the next SpMV on a block's interior rows inside each grid
                         // barrier (chunked row order, no Neumann); 0: plain barriers
   int halo;             // max |col - row| of A: rows farther than this from a block's chunk
@@ -298,6 +300,131 @@ __device__ __forceinline__ T minv_local(const SolverParams<T, VR>& p, T v, int i
   return (p.prec == 1 && !SCALAR) ? T(dinv_at(p, i) * v) : v;
 }
 
+// One Jacobi sweep of the Neumann polynomial on four rows per thread with the operands
+// staged in shared memory: out = D^{-1}src + D^{-1}(src - V src) (j = 1, V = A D^{-1}) or
+// out = prev + D^{-1}(src - V prev) (j > 1, V = A), the same per-row products in the same
+// order as the register form.  Each block walks its trips (rows base .. base+R-1) through an
+// S-stage pipeline: while trip k is computed from shared memory, the copies of trips
+// k+1 .. k+S-1 are in flight (cp.async), so the loads wait in the memory system rather than
+// in registers.  128-bit shared reads at a 16-byte thread stride are conflict-free; the
+// couplings within +-3 rows come from the own quad and the neighbouring lanes' quads
+// (shuffles), the lanes at a warp's ends read the one value beyond it from shared memory.
+template <int S, typename VR, typename Team>
+__device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team, const StageLayout& L, float* buf,
+                             int j, const float* src, const float* prev, float* out) {
+  const MatView<float>& V = j == 1 ? p.At : p.Au;
+  const float* gin = j == 1 ? src : prev;        // the gathered vector
+  const int n = p.n, R = L.R, H = L.H, row1 = team.end;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const float di = p.dinv_c;
+  int ntrips = 0;
+  for (int b = team.first4; b < row1; b += team.stride4) ++ntrips;
+  auto window = [&](float* dst, const float* v, int lo, int count) {   // rows lo .. lo+count-1, in range
+    for (int c = tid; c < count / 4; c += nt) {
+      const int row = lo + 4 * c;
+      if (row >= 0 && row < n) cp_async16(dst + 4 * c, v + row);   // n and lo multiples of 4
+    }
+  };
+  auto issue = [&](int k) {
+    float* st = buf + (size_t)(k % S) * L.stage_f;
+    const int base = team.first4 + k * team.stride4;
+    window(st, gin, base - H, R + 2 * H);
+    for (int f = 0; f < L.nfar; ++f) window(st + (R + 2 * H) + f * R, gin, base + L.far[f], R);
+    if (j > 1) window(st + L.src_f, src, base, R);
+    unsigned short* mk = reinterpret_cast<unsigned short*>(st + L.mask_f);
+    for (int c = tid; c < R / 4; c += nt) {          // 4 masks per 8-byte copy (base: a multiple of 4)
+      const int row = base + 4 * c;
+      if (row < n) cp_async8(mk + 4 * c, p.Au.mask + row);
+    }
+  };
+  // per offset of V: where its neighbours sit in a stage, relative to the thread's 4 rows
+  __shared__ int s_base[kMaxDiag];
+  if (tid < V.ndiag) {
+    const int off = V.off[tid];
+    int base = H + off;
+    if (off < -R || off > R) {
+      int f = 0;
+      while (f < L.nfar - 1 && L.far[f] != off) ++f;
+      base = (R + 2 * H) + f * R;
+    }
+    s_base[tid] = base;
+  }
+  const unsigned lane = tid & 31u;
+  for (int k = 0; k < S - 1; ++k) {
+    if (k < ntrips) issue(k);
+    cp_async_commit();
+  }
+  for (int k = 0; k < ntrips; ++k) {
+    if (k + S - 1 < ntrips) issue(k + S - 1);
+    cp_async_commit();
+    cp_async_wait<S - 1>();
+    __syncthreads();
+    const float* st = buf + (size_t)(k % S) * L.stage_f;
+    const int base = team.first4 + k * team.stride4;
+    const int i0 = base + 4 * tid;
+    const float4 own4 = *reinterpret_cast<const float4*>(st + H + 4 * tid);
+    const float own[4] = {own4.x, own4.y, own4.z, own4.w};
+    const float prv3 = __shfl_up_sync(kFull, own[3], 1), prv2 = __shfl_up_sync(kFull, own[2], 1);
+    const float prv1 = __shfl_up_sync(kFull, own[1], 1);
+    const float nxt0 = __shfl_down_sync(kFull, own[0], 1), nxt1 = __shfl_down_sync(kFull, own[1], 1);
+    const float nxt2 = __shfl_down_sync(kFull, own[2], 1);
+    if (i0 < row1) {
+      const uint2 mu = *reinterpret_cast<const uint2*>(reinterpret_cast<const unsigned short*>(st + L.mask_f) + 4 * tid);
+      const unsigned mk[4] = {mu.x & 0xffffu, mu.x >> 16, mu.y & 0xffffu, mu.y >> 16};
+      const float* ownp = st + H + 4 * tid;
+      float w[10];   // x[i0 + j] for j = -3 .. 6
+      w[0] = lane ? prv1 : ownp[-3];
+      w[1] = lane ? prv2 : ownp[-2];
+      w[2] = lane ? prv3 : ownp[-1];
+      w[3] = own[0]; w[4] = own[1]; w[5] = own[2]; w[6] = own[3];
+      w[7] = lane != 31 ? nxt0 : ownp[4];
+      w[8] = lane != 31 ? nxt1 : ownp[5];
+      w[9] = lane != 31 ? nxt2 : ownp[6];
+      float sv[4];
+      if (j == 1) {
+        sv[0] = own[0]; sv[1] = own[1]; sv[2] = own[2]; sv[3] = own[3];
+      } else {
+        const float4 s4 = *reinterpret_cast<const float4*>(st + L.src_f + 4 * tid);
+        sv[0] = s4.x; sv[1] = s4.y; sv[2] = s4.z; sv[3] = s4.w;
+      }
+      float acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = V.unit_diag ? own[q] : 0.f;
+      for (int d = 0; d < V.ndiag; ++d) {
+        const int off = V.off[d];
+        const unsigned bit = V.mbit[d];
+        const float c = V.cval[d];
+        float e[4];
+        if (off >= -3 && off <= 3) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int t = q + off + 3;   // 0 .. 9
+            e[q] = t == 0 ? w[0] : t == 1 ? w[1] : t == 2 ? w[2] : t == 3 ? w[3] : t == 4 ? w[4]
+                 : t == 5 ? w[5] : t == 6 ? w[6] : t == 7 ? w[7] : t == 8 ? w[8] : w[9];
+          }
+        } else if ((off & 3) == 0) {
+          const float4 v4 = *reinterpret_cast<const float4*>(st + s_base[d] + 4 * tid);
+          e[0] = v4.x; e[1] = v4.y; e[2] = v4.z; e[3] = v4.w;
+        } else {
+          const float* ep = st + s_base[d] + 4 * tid;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) e[q] = ep[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if ((mk[q] >> bit) & 1u) acc[q] = fma(c, e[q], acc[q]);
+      }
+      Quad<float> o;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        o.v[q] = j == 1 ? fma(di, sv[q] - acc[q], di * sv[q]) : fma(di, sv[q] - acc[q], own[q]);
+      st4(out, i0, o);
+    }
+    __syncthreads();   // the stage is refilled for trip k + S
+  }
+  cp_async_wait<0>();
+}
+
 // Neumann polynomial M^{-1} src = sum_{j<=d} (I - D^{-1}A)^j D^{-1} src by d
 // Jacobi sweeps y_1 = D^{-1}src + D^{-1}(src - (A D^{-1}) src),
 // y_j = y_{j-1} + D^{-1}(src - A y_{j-1}); one or two vectors at once.
@@ -312,6 +439,16 @@ __device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T*
   for (int j = 1; j <= d; ++j) {
     T* out0 = ((d - j) % 2 == 0) ? dst0 : p.tmpa;
     T* out1 = ((d - j) % 2 == 0) ? dst1 : p.tmpb;
+    if constexpr (VEC && std::is_same<T, float>::value) {
+      if (p.staged && !src1) {
+        extern __shared__ __align__(16) float pbcg_stage_smem[];
+        const StageLayout L = stage_layout(p.Au.off, p.Au.ndiag, 4 * (int)blockDim.x);
+        staged_sweep<3>(p, team, L, pbcg_stage_smem, j, src0, prev0, out0);
+        if (!team.sync()) return false;
+        prev0 = out0;
+        continue;
+      }
+    }
     if constexpr (VEC) {
       // four rows per thread; the stencil storage has one diagonal value (dinv_c)
       const T di = p.dinv_c;
@@ -1067,17 +1204,25 @@ __device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
 // by memory-level parallelism, so STREAM trades registers (40, with some spilling) for 48
 // resident warps per SM (three 512-thread blocks): 1173 vs 1301 us per iteration on the
 // 256^3 Neumann system (FP64 at that budget loses 12%).
-// The four-row (VEC) kernels: 512-thread blocks, one per SM (128 registers, no spills); the
-// build parameters below let a build trade registers for resident warps.
+// The four-row (VEC) kernels: 512-thread blocks, one per SM (128 registers, no spills), and
+// for a mixed solve whose working set exceeds L2 a streaming build of 768-thread blocks (80
+// registers, some spilling): 24 instead of 16 resident warps per SM, 806 vs 941 us per
+// iteration on the 256^3 Neumann system (on the L2-resident 2D system and in FP64 the
+// 512-thread build is faster: 36 vs 39 and 88 vs 105 us).  The build parameters below let a
+// build trade registers for resident warps differently.
 #ifndef PBCG_VEC_THREADS
 #define PBCG_VEC_THREADS 512
+#endif
+#ifndef PBCG_VEC_STREAM_THREADS
+#define PBCG_VEC_STREAM_THREADS 768
 #endif
 #ifndef PBCG_VEC_BLOCKS_PER_SM
 #define PBCG_VEC_BLOCKS_PER_SM 1
 #endif
 template <typename T, bool STREAM, bool VEC = false>
 struct SolverLaunch {
-  static constexpr int kThreads = VEC ? PBCG_VEC_THREADS : STREAM ? 512 : kMaxThreads;
+  static constexpr int kThreads = VEC ? (STREAM ? PBCG_VEC_STREAM_THREADS : PBCG_VEC_THREADS)
+                                      : STREAM ? 512 : kMaxThreads;
   static constexpr int kBlocksPerSM = VEC ? PBCG_VEC_BLOCKS_PER_SM : STREAM ? 3 : 1;
 };
 

@@ -250,3 +250,31 @@ def test_autograd_reuses_its_contexts_across_value_updates():
         assert np.linalg.norm(values.grad.cpu().numpy() - gvd) <= 1e-6 * np.linalg.norm(gvd), call
     assert len(pb._CACHE.entries) == 1
     pb.clear_solve_cache()
+
+
+def test_autograd_full_size_against_the_oracle_adjoint():
+    """512x512, 16 right-hand sides: the gradients of the differentiable solve against the
+    oracle's adjoint computed independently -- forward and adjoint solves by the C oracle
+    (Algorithm 2 on all host cores, tol 1e-12, the same policy) and the value gradient by
+    the oracle's formula -- to 1e-6 relative (norm-wise)."""
+    torch = torch_cuda()
+    import paper_1809_01948_gb300 as pb
+    from oracle import c_oracle
+    m = tp.problem_convdiff2d_multi(n=512, nrhs=16)
+    X, gB, gv = _loss_and_grads(torch, pb, m, tol=1e-12)
+    A = m.A.to_scipy()
+    AT = A.T.tocsr()
+    kw = dict(precond="jacobi", tol=1e-12, maxit=30000, rr_period=100, rr_theta=1e-3, max_restarts=3)
+    Xo = np.zeros_like(m.B)
+    Lo = np.zeros_like(m.B)
+    for c in range(m.B.shape[1]):
+        Xo[:, c], r = c_oracle.pbicgstab(A, m.B[:, c], **kw)
+        assert r["status"] == "OK", (c, r)
+    G = 2.0 * (Xo - m.X_target)
+    for c in range(m.B.shape[1]):
+        Lo[:, c], r = c_oracle.pbicgstab(AT, G[:, c], **kw)
+        assert r["status"] == "OK", (c, r)
+    gvo = adjoint.grad_values(m.A.row_ptr, m.A.col, Lo, Xo)
+    assert np.linalg.norm(X - Xo) <= 1e-6 * np.linalg.norm(Xo)
+    assert np.linalg.norm(gB - Lo) <= 1e-6 * np.linalg.norm(Lo)
+    assert np.linalg.norm(gv - gvo) <= 1e-6 * np.linalg.norm(gvo)

@@ -113,3 +113,38 @@ def test_four_row_kernels_run_where_they_apply():
     s = make_solver(ragged, fmt="dia", tol=1e-10, max_it=500)
     _, res, _, _ = gpu_solve(s, ragged.b)
     assert res.status == 0 and s.launch_info()["rows_per_thread"] == 1
+
+
+STAGED = {
+    # name: (problem, block_threads, staged): a block stages 4 x block_threads rows per trip
+    "3d_40_near": (lambda: tp.problem_convdiff3d(40), 0, True),       # offsets 1, 40, 1600 within a trip
+    "3d_40_far": (lambda: tp.problem_convdiff3d(40), 256, True),      # 1600 beyond a trip: its own window
+    "3d_34_far": (lambda: tp.problem_convdiff3d(34), 128, True),      # 34 near, 1156 far
+    "2d_130_near_odd": (lambda: tp.problem_convdiff2d(130), 64, True),    # 130 near, not a multiple of 4
+    "2d_130_far_odd": (lambda: tp.problem_convdiff2d(130), 32, False),    # 130 beyond a trip, unaligned
+    "2d_512_chunked": (lambda: tp.problem_convdiff2d(512), 0, True),      # chunked row order
+}
+
+
+@pytest.mark.parametrize("name", list(STAGED))
+def test_staged_sweeps_equal_register_sweeps(name):
+    """options.staged_sweeps: the Neumann sweeps of the mixed four-row kernels read their
+    operands from shared-memory stages instead of registers; same products in the same
+    order, so the solve is bit for bit the register form's.  Where the layout cannot stage
+    an offset the option is ignored."""
+    maker, threads, staged = STAGED[name]
+    prob = maker()
+    out = []
+    for flag in (0, 1):
+        s = make_solver(prob, fmt="csr", precision="mixed", precond="neumann", degree=2, tol=1e-9, max_it=400,
+                        rr_period=50, block_threads=threads, staged_sweeps=flag)
+        x, res, its, hist = gpu_solve(s, prob.b, K=5, hist_len=40)
+        info = s.launch_info()
+        assert info["rows_per_thread"] == 4
+        assert info["staged_sweeps"] == (1 if flag and staged else 0)
+        out.append((x, res, its, hist))
+    (x1, r1, i1, h1), (x2, r2, i2, h2) = out
+    assert r1.status == r2.status and r1.iterations == r2.iterations and r1.n_replacements == r2.n_replacements
+    assert np.array_equal(x1, x2)
+    assert np.array_equal(i1, i2)
+    assert np.array_equal(h1, h2, equal_nan=True)
