@@ -190,13 +190,15 @@ typedef struct pbcg_options {
                               bandwidth below half a chunk), no or Jacobi preconditioning,
                               Algorithm 2 without rr_auto                               */
   int32_t staged_sweeps;   /* single-system mixed solve with the four-row kernels and a
-                              Neumann preconditioner on stencil storage: > 0 stages the
-                              operands of the preconditioner's Jacobi sweeps in shared
-                              memory through a three-stage asynchronous-copy pipeline
-                              (same products in the same order as the register form);
-                              0 = off.  Ignored where it does not apply (offsets beyond
-                              4 x block_threads rows must be multiples of 4, and three
-                              stages must fit the block's shared memory)               */
+                              Neumann preconditioner on stencil storage: the Jacobi sweeps
+                              of the preconditioner read their operands from shared-memory
+                              stages that bulk copies (TMA) fill three trips ahead, instead
+                              of from registers (same products in the same order).  0 =
+                              automatic (on when a sweep's operands, 14 bytes per row,
+                              exceed L2), > 0 = on, < 0 = off.  Ignored where it does not
+                              apply (block_threads a multiple of 32; offsets beyond 4 x
+                              block_threads rows multiples of 4; three stages must fit the
+                              block's shared memory)                                    */
 } pbcg_options;
 
 typedef struct pbcg_result {

@@ -183,27 +183,66 @@ __device__ __forceinline__ Quad<Acc> quad_dot(const MatView<V>& A, const X* __re
   return acc;
 }
 
-// ---------------------------------------------------------------- asynchronous copies
-// cp.async (global -> shared, no registers held while the copy is in flight), committed in
-// groups; cp.async.wait_group N returns once at most N of this thread's groups are pending.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+// ---------------------------------------------------------------- time
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
+
+// ---------------------------------------------------------------- bulk copies (TMA, untiled)
+// One thread moves a contiguous range global -> shared with cp.async.bulk; the copy counts
+// its bytes off an mbarrier (complete_tx), which the consumers wait on with a phase parity.
+__device__ __forceinline__ unsigned smem_addr(const void* q) { return (unsigned)__cvta_generic_to_shared(q); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for the phase with the given parity: false after timeout_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  unsigned spins = 0;
+  while (!mbar_try_wait(bar, parity))
+    if ((++spins & 15u) == 0 && global_ns() - t0 > timeout_ns) return false;
+  return true;
+}
+// bytes: a multiple of 16; dst and src 16-byte aligned.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// Generic-proxy writes (earlier plain stores, seen through a grid barrier) before async-proxy
+// reads of global memory; an initialised mbarrier before the async proxy signals it.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Shared-memory layout of one stage of the staged stencil sweeps (four rows per thread, R =
 // 4 x threads rows per trip), the same on the host (dynamic shared memory size) and the
 // device: a near window of the gathered vector, rows [base - H, base + R + H) with H the
 // largest offset of magnitude <= R rounded up to 4 (at least 4); one R-row window per
 // farther offset (at base + offset, which must be a multiple of 4); the R own rows of the
-// source vector; the R row masks.  Sizes in floats; a stage is a multiple of 16 bytes.
+// source vector; R + 8 row masks from the multiple of 8 at or below base (16-byte bulk
+// copies; the mask array is padded to a multiple of 8 rows plus 8).  Sizes in floats;
+// every part starts on a 16-byte boundary.
 struct StageLayout {
   int R, H, nfar;
   int far[kMaxDiag];
@@ -211,8 +250,7 @@ struct StageLayout {
   int ok;                       // 0: an offset this layout cannot stage
 };
 
-__host__ __device__ inline StageLayout stage_layout(const int* off, int ndiag, int R) {
-  StageLayout L;
+__host__ __device__ inline void stage_layout(StageLayout& L, const int* off, int ndiag, int R) {
   L.R = R;
   L.H = 0;
   L.nfar = 0;
@@ -228,11 +266,10 @@ __host__ __device__ inline StageLayout stage_layout(const int* off, int ndiag, i
   }
   L.H = (L.H + 3) / 4 * 4;
   if (L.H < 4) L.H = 4;   // the sweep reads up to 3 rows beyond a warp's first and last quad
+  if (R % 8 != 0) L.ok = 0;
   L.src_f = (R + 2 * L.H) + L.nfar * R;
   L.mask_f = L.src_f + R;
-  L.stage_f = L.mask_f + R / 2;          // R 16-bit masks
-  L.stage_f = (L.stage_f + 3) / 4 * 4;
-  return L;
+  L.stage_f = L.mask_f + (R + 8) / 2;    // R + 8 16-bit masks
 }
 
 // Hint: bring the 128-byte line holding *ptr into L2 (no register is written, so a
@@ -243,12 +280,6 @@ __device__ __forceinline__ void prefetch_l2(const V* ptr) {
 }
 
 // ---------------------------------------------------------------- timing / sync
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -304,125 +304,150 @@ __device__ __forceinline__ T minv_local(const SolverParams<T, VR>& p, T v, int i
 // staged in shared memory: out = D^{-1}src + D^{-1}(src - V src) (j = 1, V = A D^{-1}) or
 // out = prev + D^{-1}(src - V prev) (j > 1, V = A), the same per-row products in the same
 // order as the register form.  Each block walks its trips (rows base .. base+R-1) through an
-// S-stage pipeline: while trip k is computed from shared memory, the copies of trips
-// k+1 .. k+S-1 are in flight (cp.async), so the loads wait in the memory system rather than
-// in registers.  128-bit shared reads at a 16-byte thread stride are conflict-free; the
+// S-stage pipeline: thread 0 moves the windows of trip k+S-1 with bulk copies (TMA, one
+// instruction per contiguous window, completing on the stage's mbarrier) while the block
+// computes trip k from shared memory, so the loads wait in the copy engine rather than in
+// registers.  128-bit shared reads at a 16-byte thread stride are conflict-free; the
 // couplings within +-3 rows come from the own quad and the neighbouring lanes' quads
 // (shuffles), the lanes at a warp's ends read the one value beyond it from shared memory.
+// A stage wait that runs past timeout_ns sets the error flag; the block then waits (bounded)
+// for its copies in flight and returns, and the grid barrier that follows reports it.
 template <int S, typename VR, typename Team>
-__device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team, const StageLayout& L, float* buf,
-                             int j, const float* src, const float* prev, float* out) {
+__device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team, float* buf, int j, const float* src,
+                             const float* prev, float* out) {
   const MatView<float>& V = j == 1 ? p.At : p.Au;
   const float* gin = j == 1 ? src : prev;        // the gathered vector
-  const int n = p.n, R = L.R, H = L.H, row1 = team.end;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const float di = p.dinv_c;
-  int ntrips = 0;
-  for (int b = team.first4; b < row1; b += team.stride4) ++ntrips;
-  auto window = [&](float* dst, const float* v, int lo, int count) {   // rows lo .. lo+count-1, in range
-    for (int c = tid; c < count / 4; c += nt) {
-      const int row = lo + 4 * c;
-      if (row >= 0 && row < n) cp_async16(dst + 4 * c, v + row);   // n and lo multiples of 4
-    }
-  };
-  auto issue = [&](int k) {
-    float* st = buf + (size_t)(k % S) * L.stage_f;
-    const int base = team.first4 + k * team.stride4;
-    window(st, gin, base - H, R + 2 * H);
-    for (int f = 0; f < L.nfar; ++f) window(st + (R + 2 * H) + f * R, gin, base + L.far[f], R);
-    if (j > 1) window(st + L.src_f, src, base, R);
-    unsigned short* mk = reinterpret_cast<unsigned short*>(st + L.mask_f);
-    for (int c = tid; c < R / 4; c += nt) {          // 4 masks per 8-byte copy (base: a multiple of 4)
-      const int row = base + 4 * c;
-      if (row < n) cp_async8(mk + 4 * c, p.Au.mask + row);
-    }
-  };
-  // per offset of V: where its neighbours sit in a stage, relative to the thread's 4 rows
+  const int n = p.n, row1 = team.end;
+  const int tid = threadIdx.x;
+  const int nmask = ((n + 7) & ~7) + 8;          // padded length of the mask array
+  __shared__ StageLayout s_lay;
   __shared__ int s_base[kMaxDiag];
-  if (tid < V.ndiag) {
+  __shared__ __align__(8) unsigned long long s_bar[S];
+  __shared__ int s_fail;
+  if (tid == 0) {
+    stage_layout(s_lay, p.Au.off, p.Au.ndiag, 4 * (int)blockDim.x);
+    for (int q = 0; q < S; ++q) mbar_init(&s_bar[q], 1);
+    fence_proxy_async_smem();
+    fence_proxy_async_global();   // the previous sweep's plain stores, before bulk reads
+    s_fail = 0;
+  }
+  __syncthreads();
+  const int R = s_lay.R, H = s_lay.H, nearw = R + 2 * s_lay.H;
+  if (tid < V.ndiag) {   // where offset d's neighbours of the thread's rows sit in a stage
     const int off = V.off[tid];
     int base = H + off;
     if (off < -R || off > R) {
       int f = 0;
-      while (f < L.nfar - 1 && L.far[f] != off) ++f;
-      base = (R + 2 * H) + f * R;
+      while (f < s_lay.nfar - 1 && s_lay.far[f] != off) ++f;
+      base = nearw + f * R;
     }
     s_base[tid] = base;
   }
-  const unsigned lane = tid & 31u;
-  for (int k = 0; k < S - 1; ++k) {
-    if (k < ntrips) issue(k);
-    cp_async_commit();
-  }
-  for (int k = 0; k < ntrips; ++k) {
-    if (k + S - 1 < ntrips) issue(k + S - 1);
-    cp_async_commit();
-    cp_async_wait<S - 1>();
-    __syncthreads();
-    const float* st = buf + (size_t)(k % S) * L.stage_f;
+  int ntrips = 0;
+  for (int b = team.first4; b < row1; b += team.stride4) ++ntrips;
+
+  // thread 0: the windows of trip k into stage k % S, clipped to the vectors' rows
+  auto issue = [&](int k) {
+    float* st = buf + (size_t)(k % S) * s_lay.stage_f;
+    unsigned long long* bar = &s_bar[k % S];
     const int base = team.first4 + k * team.stride4;
-    const int i0 = base + 4 * tid;
-    const float4 own4 = *reinterpret_cast<const float4*>(st + H + 4 * tid);
-    const float own[4] = {own4.x, own4.y, own4.z, own4.w};
-    const float prv3 = __shfl_up_sync(kFull, own[3], 1), prv2 = __shfl_up_sync(kFull, own[2], 1);
-    const float prv1 = __shfl_up_sync(kFull, own[1], 1);
-    const float nxt0 = __shfl_down_sync(kFull, own[0], 1), nxt1 = __shfl_down_sync(kFull, own[1], 1);
-    const float nxt2 = __shfl_down_sync(kFull, own[2], 1);
-    if (i0 < row1) {
-      const uint2 mu = *reinterpret_cast<const uint2*>(reinterpret_cast<const unsigned short*>(st + L.mask_f) + 4 * tid);
-      const unsigned mk[4] = {mu.x & 0xffffu, mu.x >> 16, mu.y & 0xffffu, mu.y >> 16};
-      const float* ownp = st + H + 4 * tid;
-      float w[10];   // x[i0 + j] for j = -3 .. 6
-      w[0] = lane ? prv1 : ownp[-3];
-      w[1] = lane ? prv2 : ownp[-2];
-      w[2] = lane ? prv3 : ownp[-1];
-      w[3] = own[0]; w[4] = own[1]; w[5] = own[2]; w[6] = own[3];
-      w[7] = lane != 31 ? nxt0 : ownp[4];
-      w[8] = lane != 31 ? nxt1 : ownp[5];
-      w[9] = lane != 31 ? nxt2 : ownp[6];
-      float sv[4];
-      if (j == 1) {
-        sv[0] = own[0]; sv[1] = own[1]; sv[2] = own[2]; sv[3] = own[3];
-      } else {
-        const float4 s4 = *reinterpret_cast<const float4*>(st + L.src_f + 4 * tid);
-        sv[0] = s4.x; sv[1] = s4.y; sv[2] = s4.z; sv[3] = s4.w;
-      }
-      float acc[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = V.unit_diag ? own[q] : 0.f;
-      for (int d = 0; d < V.ndiag; ++d) {
-        const int off = V.off[d];
-        const unsigned bit = V.mbit[d];
-        const float c = V.cval[d];
-        float e[4];
-        if (off >= -3 && off <= 3) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int t = q + off + 3;   // 0 .. 9
-            e[q] = t == 0 ? w[0] : t == 1 ? w[1] : t == 2 ? w[2] : t == 3 ? w[3] : t == 4 ? w[4]
-                 : t == 5 ? w[5] : t == 6 ? w[6] : t == 7 ? w[7] : t == 8 ? w[8] : w[9];
-          }
-        } else if ((off & 3) == 0) {
-          const float4 v4 = *reinterpret_cast<const float4*>(st + s_base[d] + 4 * tid);
-          e[0] = v4.x; e[1] = v4.y; e[2] = v4.z; e[3] = v4.w;
-        } else {
-          const float* ep = st + s_base[d] + 4 * tid;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) e[q] = ep[q];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if ((mk[q] >> bit) & 1u) acc[q] = fma(c, e[q], acc[q]);
-      }
-      Quad<float> o;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        o.v[q] = j == 1 ? fma(di, sv[q] - acc[q], di * sv[q]) : fma(di, sv[q] - acc[q], own[q]);
-      st4(out, i0, o);
+    const int mlo = base & ~7;
+    const int mhi = min(mlo + R + 8, nmask);
+    unsigned bytes = 0;
+    for (int go = 0; go < 2; ++go) {
+      if (go) mbar_arrive_expect_tx(bar, bytes);
+      auto win = [&](float* dst, const float* v, int lo, int cnt) {
+        const int a0 = max(lo, 0), a1 = min(lo + cnt, n);   // multiples of 4
+        if (a1 <= a0) return;
+        if (go) bulk_copy_g2s(dst + (a0 - lo), v + a0, (unsigned)(a1 - a0) * 4u, bar);
+        else bytes += (unsigned)(a1 - a0) * 4u;
+      };
+      win(st, gin, base - H, nearw);
+      for (int f = 0; f < s_lay.nfar; ++f) win(st + nearw + f * R, gin, base + s_lay.far[f], R);
+      if (j > 1) win(st + s_lay.src_f, src, base, R);
+      if (go) bulk_copy_g2s(st + s_lay.mask_f, p.Au.mask + mlo, (unsigned)(mhi - mlo) * 2u, bar);
+      else bytes += (unsigned)(mhi - mlo) * 2u;
     }
-    __syncthreads();   // the stage is refilled for trip k + S
+  };
+  if (tid == 0)
+    for (int k = 0; k < S - 1 && k < ntrips; ++k) issue(k);
+  const unsigned lane = tid & 31u;
+  int k = 0;
+  for (; k < ntrips; ++k) {
+    if (tid == 0 && k + S - 1 < ntrips) issue(k + S - 1);
+    bool ok = mbar_wait(&s_bar[k % S], (unsigned)(k / S) & 1u, p.timeout_ns);
+    ok = __all_sync(kFull, ok);
+    if (!ok) s_fail = 1;
+    if (ok) {
+      const float* st = buf + (size_t)(k % S) * s_lay.stage_f;
+      const int base = team.first4 + k * team.stride4;
+      const int i0 = base + 4 * tid;
+      const float* ownp = st + H + 4 * tid;
+      const float4 own4 = *reinterpret_cast<const float4*>(ownp);
+      const float prv1 = __shfl_up_sync(kFull, own4.y, 1), prv2 = __shfl_up_sync(kFull, own4.z, 1);
+      const float prv3 = __shfl_up_sync(kFull, own4.w, 1);
+      const float nxt0 = __shfl_down_sync(kFull, own4.x, 1), nxt1 = __shfl_down_sync(kFull, own4.y, 1);
+      const float nxt2 = __shfl_down_sync(kFull, own4.z, 1);
+      if (i0 < row1) {
+        const unsigned short* mrow =
+            reinterpret_cast<const unsigned short*>(st + s_lay.mask_f) + (base - (base & ~7)) + 4 * tid;
+        const uint2 mu = *reinterpret_cast<const uint2*>(mrow);
+        const unsigned m0 = mu.x & 0xffffu, m1 = mu.x >> 16, m2 = mu.y & 0xffffu, m3 = mu.y >> 16;
+        // x[i0 + t] for t = -3 .. 6
+        const float wm3 = lane ? prv1 : ownp[-3], wm2 = lane ? prv2 : ownp[-2], wm1 = lane ? prv3 : ownp[-1];
+        const float w4 = lane != 31 ? nxt0 : ownp[4], w5 = lane != 31 ? nxt1 : ownp[5];
+        const float w6 = lane != 31 ? nxt2 : ownp[6];
+        const float w0 = own4.x, w1 = own4.y, w2 = own4.z, w3 = own4.w;
+        auto pick = [&](int t) {   // x[i0 + t], -3 <= t <= 6
+          return t == -3 ? wm3 : t == -2 ? wm2 : t == -1 ? wm1 : t == 0 ? w0 : t == 1 ? w1 : t == 2 ? w2
+               : t == 3 ? w3 : t == 4 ? w4 : t == 5 ? w5 : w6;
+        };
+        float4 sv = own4;
+        if (j > 1) sv = *reinterpret_cast<const float4*>(st + s_lay.src_f + 4 * tid);
+        float a0 = V.unit_diag ? w0 : 0.f, a1 = V.unit_diag ? w1 : 0.f;
+        float a2 = V.unit_diag ? w2 : 0.f, a3 = V.unit_diag ? w3 : 0.f;
+        for (int d = 0; d < V.ndiag; ++d) {
+          const int off = V.off[d];
+          const unsigned bit = V.mbit[d];
+          const float c = V.cval[d];
+          float e0, e1, e2, e3;
+          if (off >= -3 && off <= 3) {
+            e0 = pick(off); e1 = pick(off + 1); e2 = pick(off + 2); e3 = pick(off + 3);
+          } else if ((off & 3) == 0) {
+            const float4 v4 = *reinterpret_cast<const float4*>(st + s_base[d] + 4 * tid);
+            e0 = v4.x; e1 = v4.y; e2 = v4.z; e3 = v4.w;
+          } else {
+            const float* ep = st + s_base[d] + 4 * tid;
+            e0 = ep[0]; e1 = ep[1]; e2 = ep[2]; e3 = ep[3];
+          }
+          if ((m0 >> bit) & 1u) a0 = fma(c, e0, a0);
+          if ((m1 >> bit) & 1u) a1 = fma(c, e1, a1);
+          if ((m2 >> bit) & 1u) a2 = fma(c, e2, a2);
+          if ((m3 >> bit) & 1u) a3 = fma(c, e3, a3);
+        }
+        const float di = p.dinv_c;
+        Quad<float> o;
+        if (j == 1) {
+          o.v[0] = fma(di, sv.x - a0, di * sv.x); o.v[1] = fma(di, sv.y - a1, di * sv.y);
+          o.v[2] = fma(di, sv.z - a2, di * sv.z); o.v[3] = fma(di, sv.w - a3, di * sv.w);
+        } else {
+          o.v[0] = fma(di, sv.x - a0, w0); o.v[1] = fma(di, sv.y - a1, w1);
+          o.v[2] = fma(di, sv.z - a2, w2); o.v[3] = fma(di, sv.w - a3, w3);
+        }
+        st4(out, i0, o);
+      }
+    }
+    __syncthreads();   // the stage is refilled for trip k + S; s_fail is settled
+    if (s_fail) break;
   }
-  cp_async_wait<0>();
+  if (tid == 0) {
+    if (s_fail) {
+      atomicCAS(p.err, 0, (int)kTimeout);
+      const int issued = min(ntrips, k + S);   // trips 0 .. k + S - 1 were issued
+      for (int q = k; q < issued; ++q) mbar_wait(&s_bar[q % S], (unsigned)(q / S) & 1u, p.timeout_ns);
+    }
+    for (int q = 0; q < S; ++q) mbar_inval(&s_bar[q]);
+  }
 }
 
 // Neumann polynomial M^{-1} src = sum_{j<=d} (I - D^{-1}A)^j D^{-1} src by d
@@ -442,8 +467,7 @@ __device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T*
     if constexpr (VEC && std::is_same<T, float>::value) {
       if (p.staged && !src1) {
         extern __shared__ __align__(16) float pbcg_stage_smem[];
-        const StageLayout L = stage_layout(p.Au.off, p.Au.ndiag, 4 * (int)blockDim.x);
-        staged_sweep<3>(p, team, L, pbcg_stage_smem, j, src0, prev0, out0);
+        staged_sweep<3>(p, team, pbcg_stage_smem, j, src0, prev0, out0);
         if (!team.sync()) return false;
         prev0 = out0;
         continue;

@@ -156,7 +156,11 @@ pbcg_status build_stencil(pbcg_ctx* c) {
     for (int d = 0; d < c->ndiag; ++d) st.off[d] = dia.off[d] = c->offsets[d];
   }
   SCK(cudaMalloc(&mm, sizeof(unsigned long long) * 2 * kMaxDiag), "cudaMalloc min/max");
-  SCK(cudaMalloc(&mask, sizeof(unsigned short) * n), "cudaMalloc stencil mask");
+  // padded to a multiple of 8 rows plus 8 (zero masks), so that the staged sweeps move
+  // whole 16-byte groups of masks with bulk copies
+  const size_t nmask = (size_t)((n + 7) & ~7) + 8;
+  SCK(cudaMalloc(&mask, sizeof(unsigned short) * nmask), "cudaMalloc stencil mask");
+  SCK(cudaMemsetAsync(mask + n, 0, sizeof(unsigned short) * (nmask - n), s), "memset mask padding");
   SCK(cudaMemsetAsync(mm, 0xff, sizeof(unsigned long long) * kMaxDiag, s), "memset");
   SCK(cudaMemsetAsync(mm + kMaxDiag, 0, sizeof(unsigned long long) * kMaxDiag, s), "memset");
   stencil_scan_kernel<<<nb, 256, 0, s>>>(n, c->fmt, c->row_ptr, c->col, c->val64, dia, st, mm, mm + kMaxDiag, mask);

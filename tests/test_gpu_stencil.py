@@ -135,16 +135,24 @@ def test_staged_sweeps_equal_register_sweeps(name):
     maker, threads, staged = STAGED[name]
     prob = maker()
     out = []
-    for flag in (0, 1):
+    for flag in (-1, 1):
         s = make_solver(prob, fmt="csr", precision="mixed", precond="neumann", degree=2, tol=1e-9, max_it=400,
                         rr_period=50, block_threads=threads, staged_sweeps=flag)
         x, res, its, hist = gpu_solve(s, prob.b, K=5, hist_len=40)
         info = s.launch_info()
         assert info["rows_per_thread"] == 4
-        assert info["staged_sweeps"] == (1 if flag and staged else 0)
+        assert info["staged_sweeps"] == (1 if flag > 0 and staged else 0)
         out.append((x, res, its, hist))
     (x1, r1, i1, h1), (x2, r2, i2, h2) = out
     assert r1.status == r2.status and r1.iterations == r2.iterations and r1.n_replacements == r2.n_replacements
     assert np.array_equal(x1, x2)
     assert np.array_equal(i1, i2)
     assert np.array_equal(h1, h2, equal_nan=True)
+
+
+def test_staged_sweeps_automatic_rule():
+    """0 (the default) stages the sweeps only where their operands exceed L2: not at 40^3."""
+    prob = tp.problem_convdiff3d(40)
+    s = make_solver(prob, fmt="csr", precision="mixed", tol=1e-9, max_it=50)
+    gpu_solve(s, prob.b)
+    assert s.launch_info()["staged_sweeps"] == 0
