@@ -4,6 +4,7 @@
 // limit, and compensated FP32 accumulation for the mixed-precision dots.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace pbcg {
@@ -159,8 +160,8 @@ __device__ __forceinline__ Quad<Acc> quad_dot(const MatView<V>& A, const X* __re
     for (int j = 0; j < 4; ++j) acc.v[j] = Acc(0);
   }
   const int n = A.n;
-#pragma unroll 2
-  for (int d = 0; d < A.ndiag; ++d) {
+  // offset d's products
+  auto product = [&](int d) {
     const int off = A.off[d];
     const unsigned bit = A.mbit[d];
     const Acc c = Acc(A.cval[d]);
@@ -179,7 +180,35 @@ __device__ __forceinline__ Quad<Acc> quad_dot(const MatView<V>& A, const X* __re
 #pragma unroll
     for (int j = 0; j < 4; ++j)
       if ((m[j] >> bit) & 1u) acc.v[j] = fma(c, Acc(e[j]), acc.v[j]);
+  };
+  if constexpr (std::is_same<Acc, float>::value) {
+    // FP32: with the offset count known at compile time (4-7: the 2D and 3D stencils, with
+    // or without the main diagonal) the loop unrolls and the offsets become constant-bank
+    // operands whose tests are loop-invariant (measured 1% faster per iteration on the 2D
+    // mixed solve; the FP64 builds, bound by the FP64 pipe, were 1-4% slower so)
+    switch (A.ndiag) {
+      case 4:
+#pragma unroll
+        for (int d = 0; d < 4; ++d) product(d);
+        return acc;
+      case 5:
+#pragma unroll
+        for (int d = 0; d < 5; ++d) product(d);
+        return acc;
+      case 6:
+#pragma unroll
+        for (int d = 0; d < 6; ++d) product(d);
+        return acc;
+      case 7:
+#pragma unroll
+        for (int d = 0; d < 7; ++d) product(d);
+        return acc;
+      default:
+        break;
+    }
   }
+#pragma unroll 2
+  for (int d = 0; d < A.ndiag; ++d) product(d);
   return acc;
 }
 

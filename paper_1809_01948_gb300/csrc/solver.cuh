@@ -406,14 +406,19 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
         if (j > 1) sv = *reinterpret_cast<const float4*>(st + s_lay.src_f + 4 * tid);
         float a0 = V.unit_diag ? w0 : 0.f, a1 = V.unit_diag ? w1 : 0.f;
         float a2 = V.unit_diag ? w2 : 0.f, a3 = V.unit_diag ? w3 : 0.f;
-        for (int d = 0; d < V.ndiag; ++d) {
+        // offset d's products; with the offset count known at compile time (5: 2D, 7: 3D
+        // stencils) the loop unrolls, the offsets become constant-bank operands and their
+        // tests loop-invariant, which is most of a sweep's instruction count
+        auto product = [&](int d) {
           const int off = V.off[d];
           const unsigned bit = V.mbit[d];
           const float c = V.cval[d];
           float e0, e1, e2, e3;
-          if (off >= -3 && off <= 3) {
-            e0 = pick(off); e1 = pick(off + 1); e2 = pick(off + 2); e3 = pick(off + 3);
-          } else if ((off & 3) == 0) {
+          if (off == -1) { e0 = wm1; e1 = w0; e2 = w1; e3 = w2; }
+          else if (off == 1) { e0 = w1; e1 = w2; e2 = w3; e3 = w4; }
+          else if (off == 0) { e0 = w0; e1 = w1; e2 = w2; e3 = w3; }
+          else if (off >= -3 && off <= 3) { e0 = pick(off); e1 = pick(off + 1); e2 = pick(off + 2); e3 = pick(off + 3); }
+          else if ((off & 3) == 0) {
             const float4 v4 = *reinterpret_cast<const float4*>(st + s_base[d] + 4 * tid);
             e0 = v4.x; e1 = v4.y; e2 = v4.z; e3 = v4.w;
           } else {
@@ -424,6 +429,16 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
           if ((m1 >> bit) & 1u) a1 = fma(c, e1, a1);
           if ((m2 >> bit) & 1u) a2 = fma(c, e2, a2);
           if ((m3 >> bit) & 1u) a3 = fma(c, e3, a3);
+        };
+        if (V.ndiag == 7) {
+#pragma unroll
+          for (int d = 0; d < 7; ++d) product(d);
+        } else if (V.ndiag == 5) {
+#pragma unroll
+          for (int d = 0; d < 5; ++d) product(d);
+        } else {
+#pragma unroll 1
+          for (int d = 0; d < V.ndiag; ++d) product(d);
         }
         const float di = p.dinv_c;
         Quad<float> o;
