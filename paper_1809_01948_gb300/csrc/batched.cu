@@ -56,6 +56,7 @@ __device__ __forceinline__ MatView<V> csr_view(int n, const int* rp, const int* 
   m.val = val;
   m.ndiag = 0;
   m.unit_diag = 0;
+  m.pattern = 0;
   return m;
 }
 

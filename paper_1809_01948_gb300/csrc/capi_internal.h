@@ -128,6 +128,7 @@ inline MatView<V> make_stencil_view(const pbcg_ctx* c, bool hot) {
   }
   m.ndiag = k;
   m.unit_diag = (hot && c->fmt == PBCG_FMT_DIA) ? 1 : 0;
+  m.pattern = pbcg::stencil_pattern(m.off, m.ndiag);
   return m;
 }
 

@@ -39,7 +39,40 @@ struct MatView {
   int off[kMaxDiag];
   V cval[kMaxDiag];                 // stencil: the value at offset off[d]
   unsigned char mbit[kMaxDiag];     // stencil: mask bit of offset off[d]
+  int pattern;                      // stencil: stencil_pattern of the offsets (0: none)
 };
+
+// Offset patterns of the 3D and 2D stencils (with or without the main diagonal), as kinds
+// per offset in ascending order: 0 a nonzero multiple of 4 (an aligned quad), 1 / 2 / 3 the
+// offsets -1 / 0 / +1.  A pattern is named by its offset count: 7 (3D), 6 (3D without the
+// diagonal), 5 (2D), 4 (2D without the diagonal).
+__host__ __device__ constexpr int stencil_kind(int pat, int d) {
+  return pat == 7 ? (d < 2 ? 0 : d < 5 ? d - 1 : 0)
+       : pat == 6 ? (d < 2 ? 0 : d == 2 ? 1 : d == 3 ? 3 : 0)
+       : pat == 5 ? (d == 0 ? 0 : d < 4 ? d : 0)
+       : (d == 0 ? 0 : d == 1 ? 1 : d == 2 ? 3 : 0);
+}
+__host__ __device__ inline int offset_kind(int off) {
+  return off == -1 ? 1 : off == 0 ? 2 : off == 1 ? 3 : (off % 4 == 0) ? 0 : -1;
+}
+// The pattern the ascending offsets off[0 .. nd-1] follow, or 0.
+__host__ __device__ inline int stencil_pattern(const int* off, int nd) {
+  for (int q = 7; q >= 4; --q) {
+    if (nd != q) continue;
+    bool match = true;
+    for (int d = 0; d < q; ++d) match = match && offset_kind(off[d]) == stencil_kind(q, d);
+    return match ? q : 0;
+  }
+  return 0;
+}
+// f(d, kind) for d = 0 .. PAT-1 with the kind a compile-time constant.
+template <int PAT, int D = 0, typename F>
+__device__ __forceinline__ void for_pattern(F& f) {
+  if constexpr (D < PAT) {
+    f(D, std::integral_constant<int, stencil_kind(PAT, D)>{});
+    for_pattern<PAT, D + 1>(f);
+  }
+}
 
 // y_i = sum_j a_ij x_j for one row i, accumulated with FMA in type Acc, stored
 // diagonals / columns in ascending order.
@@ -182,6 +215,41 @@ __device__ __forceinline__ Quad<Acc> quad_dot(const MatView<V>& A, const X* __re
       if ((m[j] >> bit) & 1u) acc.v[j] = fma(c, Acc(e[j]), acc.v[j]);
   };
   if constexpr (std::is_same<Acc, float>::value) {
+    if (A.pattern) {
+      // FP32, a stencil pattern: the offset kinds are compile-time constants, and the -1, 0
+      // and +1 products share the quads i0-4, i0, i0+4 (loaded once, zero outside 0 .. n-1)
+      Quad<X> qm, q0, qp;
+      qm.v[0] = qm.v[1] = qm.v[2] = qm.v[3] = X(0);
+      qp = qm;
+      q0 = ld4(x, i0);
+      if (i0 >= 4) qm = ld4(x, i0 - 4);
+      if (i0 + 4 < n) qp = ld4(x, i0 + 4);
+      auto product_k = [&](int d, auto kc) {
+        constexpr int K = decltype(kc)::value;
+        const unsigned bit = A.mbit[d];
+        const Acc c = Acc(A.cval[d]);
+        X e[4];
+        if constexpr (K == 1) { e[0] = qm.v[3]; e[1] = q0.v[0]; e[2] = q0.v[1]; e[3] = q0.v[2]; }
+        else if constexpr (K == 2) { e[0] = q0.v[0]; e[1] = q0.v[1]; e[2] = q0.v[2]; e[3] = q0.v[3]; }
+        else if constexpr (K == 3) { e[0] = q0.v[1]; e[1] = q0.v[2]; e[2] = q0.v[3]; e[3] = qp.v[0]; }
+        else {
+          const int a = i0 + A.off[d];   // a multiple of 4
+          Quad<X> q;
+          q.v[0] = q.v[1] = q.v[2] = q.v[3] = X(0);
+          if (a >= 0 && a < n) q = ld4(x, a);
+          e[0] = q.v[0]; e[1] = q.v[1]; e[2] = q.v[2]; e[3] = q.v[3];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if ((m[j] >> bit) & 1u) acc.v[j] = fma(c, Acc(e[j]), acc.v[j]);
+      };
+      switch (A.pattern) {
+        case 7: for_pattern<7>(product_k); return acc;
+        case 6: for_pattern<6>(product_k); return acc;
+        case 5: for_pattern<5>(product_k); return acc;
+        default: for_pattern<4>(product_k); return acc;
+      }
+    }
     // FP32: with the offset count known at compile time (4-7: the 2D and 3D stencils, with
     // or without the main diagonal) the loop unrolls and the offsets become constant-bank
     // operands whose tests are loop-invariant (measured 1% faster per iteration on the 2D

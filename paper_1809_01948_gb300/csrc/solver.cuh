@@ -345,6 +345,9 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
   }
   int ntrips = 0;
   for (int b = team.first4; b < row1; b += team.stride4) ++ntrips;
+  // V's offsets in one of the stencil patterns: the products of a trip then carry no
+  // offset tests
+  const int pat = V.pattern;
 
   // thread 0: the windows of trip k into stage k % S, clipped to the vectors' rows
   auto issue = [&](int k) {
@@ -430,7 +433,33 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
           if ((m2 >> bit) & 1u) a2 = fma(c, e2, a2);
           if ((m3 >> bit) & 1u) a3 = fma(c, e3, a3);
         };
-        if (V.ndiag == 7) {
+        // the same products with the offset kinds fixed at compile time
+        auto product_k = [&](int d, auto kc) {
+          constexpr int K = decltype(kc)::value;
+          const unsigned bit = V.mbit[d];
+          const float c = V.cval[d];
+          float e0, e1, e2, e3;
+          if constexpr (K == 1) { e0 = wm1; e1 = w0; e2 = w1; e3 = w2; }
+          else if constexpr (K == 2) { e0 = w0; e1 = w1; e2 = w2; e3 = w3; }
+          else if constexpr (K == 3) { e0 = w1; e1 = w2; e2 = w3; e3 = w4; }
+          else {
+            const float4 v4 = *reinterpret_cast<const float4*>(st + s_base[d] + 4 * tid);
+            e0 = v4.x; e1 = v4.y; e2 = v4.z; e3 = v4.w;
+          }
+          if ((m0 >> bit) & 1u) a0 = fma(c, e0, a0);
+          if ((m1 >> bit) & 1u) a1 = fma(c, e1, a1);
+          if ((m2 >> bit) & 1u) a2 = fma(c, e2, a2);
+          if ((m3 >> bit) & 1u) a3 = fma(c, e3, a3);
+        };
+        if (pat == 7) {
+          for_pattern<7>(product_k);
+        } else if (pat == 6) {
+          for_pattern<6>(product_k);
+        } else if (pat == 5) {
+          for_pattern<5>(product_k);
+        } else if (pat == 4) {
+          for_pattern<4>(product_k);
+        } else if (V.ndiag == 7) {
 #pragma unroll
           for (int d = 0; d < 7; ++d) product(d);
         } else if (V.ndiag == 5) {
@@ -804,7 +833,7 @@ __device__ __forceinline__ void pass_b_quads(const SolverParams<T, VR>& p, const
 
 // The whole solve (Algorithm 2 + Eq. rr) for one system, executed by a team.
 template <bool AUTO, bool SCALAR, bool VEC = false, typename T, typename VR, typename Team>
-__device__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
+__device__ __forceinline__ void solve_body(const SolverParams<T, VR>& p, Team& team) {
   static_assert(!(VEC && AUTO), "the four-row passes run without the automated policy");
   using Acc = typename AccOf<T>::type;
   const int n = p.n;
