@@ -206,8 +206,9 @@ def measured_fp64_tflops(dev) -> float:
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
-def workload_setup(kind: str, grid: int, dev):
-    """The synthetic system of a workload, its solver inputs, and the byte / flop models."""
+def workload_setup(kind: str, grid: int, dev, degree: int = 2):
+    """The synthetic system of a workload, its solver inputs, and the byte / flop models
+    (degree: the Neumann degree of the 3D system)."""
     import torch
     import testproblems as tp
     if kind == "convdiff2d":
@@ -231,8 +232,8 @@ def workload_setup(kind: str, grid: int, dev):
     else:
         prob = tp.problem_convdiff3d(grid)
         mat = dict(row_ptr=torch.from_numpy(prob.A.row_ptr).to(dev), col=torch.from_numpy(prob.A.col).to(dev),
-                   val=torch.from_numpy(prob.A.val).to(dev), precond="neumann", degree=2)
-        name = "convdiff3d_%d^3_csr7_neumann2_tol1e-10" % grid
+                   val=torch.from_numpy(prob.A.val).to(dev), precond="neumann", degree=degree)
+        name = "convdiff3d_%d^3_csr7_neumann%d_tol1e-10" % (grid, degree)
         fmt = "CSR int32, 7 nnz/row, FP64 values"
         variants = {
             # FP32 recurrences restarted every 75 iterations (reading R20)
@@ -240,8 +241,8 @@ def workload_setup(kind: str, grid: int, dev):
             # the paper's periodic replacement (every 100 iterations)
             "fp64": dict(precision="fp64", rr_period=100),
         }
-        model = dict(bpr=lambda prec, st: bytes_per_row_iteration_neumann(prec, storage=st),
-                     flops=fp64_flops_per_row_iteration_neumann())
+        model = dict(bpr=lambda prec, st: bytes_per_row_iteration_neumann(prec, degree=degree, storage=st),
+                     flops=fp64_flops_per_row_iteration_neumann(degree=degree))
     return prob, mat, name, fmt, variants, model
 
 
@@ -301,7 +302,7 @@ def run_gpu(args):
 
     def measure(kind, grid, headline):
         nonlocal sampler_on
-        prob, mat, name, fmt, variants, model = workload_setup(kind, grid, dev)
+        prob, mat, name, fmt, variants, model = workload_setup(kind, grid, dev, args.degree)
         b = torch.from_numpy(prob.b).to(dev)
         n = prob.A.n
         if args.only:
@@ -672,6 +673,8 @@ def main():
     ap.add_argument("--grid", type=int, default=0, help="2D grid size per dimension (profiling of smaller cases)")
     ap.add_argument("--grid3", type=int, default=0, help="3D grid size per dimension (profiling of smaller cases)")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D 256^3 workload")
+    ap.add_argument("--degree", type=int, default=2,
+                    help="Neumann degree of the 3D system (profiling of sweep-dominated launches)")
     ap.add_argument("--workload", default="convdiff2d", choices=["convdiff2d", "convdiff3d", "batched", "autograd"],
                     help="convdiff2d (default): 2D convection-diffusion 1024^2 DIA headline, with the 3D 256^3 CSR "
                          "Neumann-2 system measured alongside; convdiff3d: the 3D system alone; batched: 512 banded "
