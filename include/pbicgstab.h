@@ -360,7 +360,8 @@ const char* pbicgstab_last_error(void);
  *   col / val  col[nnz_off[k] + e], val[nnz_off[k] + e] with LOCAL column
  *              indices 0 .. n_k-1.
  * row_off and nnz_off (n_sys + 1 int64 each) are HOST arrays; row_ptr, col, val
- * are device arrays.  Preconditioner: NONE or JACOBI (per system). */
+ * are device arrays.  Preconditioner (per system, Section 2 of the paper): NONE, JACOBI,
+ * or NEUMANN of `degree` 1..8 (the Jacobi sweeps of the single-system solver). */
 typedef struct pbcg_batch {
   int32_t n_sys;
   int32_t val_dtype;        /* pbcg_dtype */
@@ -369,8 +370,8 @@ typedef struct pbcg_batch {
   const int32_t* row_ptr;   /* device */
   const int32_t* col;       /* device */
   const void* val;          /* device */
-  int32_t precond;          /* PBCG_PREC_NONE or PBCG_PREC_JACOBI */
-  int32_t reserved0;
+  int32_t precond;          /* PBCG_PREC_NONE, PBCG_PREC_JACOBI or PBCG_PREC_NEUMANN */
+  int32_t degree;           /* Neumann degree 1..8 (ignored for NONE and JACOBI) */
 } pbcg_batch;
 
 /* Per-system outputs, HOST arrays of n_sys entries (any may be NULL). */

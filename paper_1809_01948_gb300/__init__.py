@@ -298,7 +298,8 @@ class BatchSolver:
     kernel; mixed precision).
     """
 
-    def __init__(self, row_off, nnz_off, row_ptr, col, val, precond: str = "jacobi", precision: str = "mixed",
+    def __init__(self, row_off, nnz_off, row_ptr, col, val, precond: str = "jacobi", degree: int = 0,
+                 precision: str = "mixed",
                  tol: float = 1e-8, max_it: int = 1000, rr_period: int = 0, rr_theta: float = 0.0,
                  grid_blocks: int = 0, block_threads: int = 0, max_restarts: int = 0, cluster_blocks: int = 0,
                  lanes_per_row: int = 0, build: str = "auto", restart_period: int = 0, stag_window: int = 0,
@@ -327,6 +328,7 @@ class BatchSolver:
         bt.nnz_off = self.nnz_off.ctypes.data_as(C.c_void_p)
         bt.row_ptr, bt.col, bt.val = _ptr(row_ptr), _ptr(col), _ptr(val)
         bt.precond = _PREC[precond]
+        bt.degree = int(degree)
         self.opt = capi.Options()
         _check(lib.pbicgstab_default_options(C.byref(self.opt)), "default_options")
         self.opt.precision = _PRECISION[precision]

@@ -61,7 +61,7 @@ class Result(C.Structure):
 class Batch(C.Structure):
     _fields_ = [("n_sys", C.c_int32), ("val_dtype", C.c_int32), ("row_off", C.c_void_p), ("nnz_off", C.c_void_p),
                 ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p), ("precond", C.c_int32),
-                ("reserved0", C.c_int32)]
+                ("degree", C.c_int32)]
 
 
 class BatchResult(C.Structure):

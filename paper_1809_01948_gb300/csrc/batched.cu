@@ -35,6 +35,7 @@ struct BatchDev {
   DevResult* res;             // n_sys
   unsigned* counter;
   int prec;
+  int degree;                 // Neumann degree (prec == PBCG_PREC_NEUMANN)
   double tol;
   int max_it;
   int rr_period;
@@ -77,7 +78,7 @@ __device__ void build_params(const BatchDev& d, int k, SolverParams<T, VR>& p) {
   p.dinv_x = 1.0;
   p.prefetch = 0;
   p.prec = d.prec;
-  p.degree = 0;
+  p.degree = d.degree;
   p.b = d.b + r0;
   p.x = d.x + r0;
   T* v = (T*)d.vecs + r0;
@@ -285,7 +286,7 @@ __global__ void batch_prepare_kernel(int n_sys, const long long* row_off, const 
 struct pbcg_batch_ctx {
   int n_sys = 0;
   long long total_rows = 0, total_nnz = 0;
-  int precision = 0, vr_f32 = 0, prec = 0;
+  int precision = 0, vr_f32 = 0, prec = 0, degree = 0;
   pbcg_options opt{};
   cudaStream_t stream = nullptr, cap_stream = nullptr;
   long long *row_off = nullptr, *nnz_off = nullptr;
@@ -362,6 +363,7 @@ static BatchDev make_dev(pbcg_batch_ctx* c, const double* b, double* x, int lane
   d.res = c->dres;
   d.counter = c->counter;
   d.prec = c->prec;
+  d.degree = c->degree;
   d.tol = c->opt.tol;
   d.max_it = c->opt.max_it;
   d.rr_period = c->opt.rr_period;
@@ -514,8 +516,10 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
   if (B->n_sys < 1 || !B->row_off || !B->nnz_off || !B->row_ptr || !B->col || !B->val)
     return set_error(PBCG_INVALID_ARG, "batch needs n_sys >= 1 and all arrays");
   if (B->val_dtype != PBCG_F64 && B->val_dtype != PBCG_F32) return set_error(PBCG_INVALID_ARG, "unknown dtype");
-  if (B->precond != PBCG_PREC_NONE && B->precond != PBCG_PREC_JACOBI)
-    return set_error(PBCG_INVALID_ARG, "batched solves support NONE and JACOBI preconditioners");
+  if (B->precond != PBCG_PREC_NONE && B->precond != PBCG_PREC_JACOBI && B->precond != PBCG_PREC_NEUMANN)
+    return set_error(PBCG_INVALID_ARG, "batched solves support NONE, JACOBI and NEUMANN preconditioners");
+  if (B->precond == PBCG_PREC_NEUMANN && (B->degree < 1 || B->degree > 8))
+    return set_error(PBCG_INVALID_ARG, "Neumann degree must be in [1, 8]");
   if (opt->precision != PBCG_FP64 && opt->precision != PBCG_MIXED) return set_error(PBCG_INVALID_ARG, "bad precision");
   if (opt->max_it < 0 || !(opt->tol >= 0.0) || opt->rr_period < 0 || !(opt->rr_theta >= 0.0 && opt->rr_theta < 1.0) ||
       opt->rr_auto != 0)
@@ -557,6 +561,7 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
   c->precision = opt->precision;
   c->vr_f32 = B->val_dtype == PBCG_F32;
   c->prec = B->precond;
+  c->degree = B->precond == PBCG_PREC_NEUMANN ? B->degree : 0;
   c->opt = *opt;
   c->stream = (cudaStream_t)stream;
   const size_t es = c->precision == PBCG_MIXED ? 4 : 8;
@@ -593,7 +598,8 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
   }
   CKB(cudaMemsetAsync(c->flags, 0, sizeof(int), s), "memset");
   const unsigned nb = (unsigned)((R + 255) / 256);
-  const int jac = c->prec == PBCG_PREC_JACOBI;
+  // Jacobi and Neumann both need D^{-1} and the folded A D^{-1} (the first Neumann sweep)
+  const int jac = c->prec != PBCG_PREC_NONE;
   batch_validate_kernel<<<nb, 256, 0, s>>>(ns, c->row_off, c->nnz_off, c->row_ptr, c->col, c->valR, c->vr_f32, jac,
                                            c->flags, c->diag);
   CKB(cudaGetLastError(), "batch validation launch");
@@ -605,7 +611,7 @@ extern "C" pbcg_status pbicgstab_batch_create(pbcg_batch_ctx** out, const pbcg_b
     if (hflags & 1) return set_error(PBCG_INVALID_ARG, "a system's row_ptr is not monotone from 0 to its nnz");
     if (hflags & 2) return set_error(PBCG_INVALID_ARG, "a column index is out of range or not increasing");
     if (hflags & 4) return set_error(PBCG_INVALID_ARG, "a matrix value is not finite");
-    return set_error(PBCG_INVALID_ARG, "Jacobi needs a non-zero diagonal in every row");
+    return set_error(PBCG_INVALID_ARG, "Jacobi and Neumann need a non-zero diagonal in every row");
   }
   // values in T: the unfolded copy (mixed with FP64 input, or FP64 with FP32 input) and A D^{-1}
   const bool need_au = (c->precision == PBCG_MIXED) != (bool)c->vr_f32;

@@ -387,23 +387,30 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
       const int i0 = base + 4 * tid;
       const float* ownp = st + H + 4 * tid;
       const float4 own4 = *reinterpret_cast<const float4*>(ownp);
-      const float prv1 = __shfl_up_sync(kFull, own4.y, 1), prv2 = __shfl_up_sync(kFull, own4.z, 1);
       const float prv3 = __shfl_up_sync(kFull, own4.w, 1);
-      const float nxt0 = __shfl_down_sync(kFull, own4.x, 1), nxt1 = __shfl_down_sync(kFull, own4.y, 1);
-      const float nxt2 = __shfl_down_sync(kFull, own4.z, 1);
+      const float nxt0 = __shfl_down_sync(kFull, own4.x, 1);
+      float prv1 = 0.f, prv2 = 0.f, nxt1 = 0.f, nxt2 = 0.f;   // the +-2, +-3 couplings: general offsets only
+      if (pat == 0) {
+        prv1 = __shfl_up_sync(kFull, own4.y, 1);
+        prv2 = __shfl_up_sync(kFull, own4.z, 1);
+        nxt1 = __shfl_down_sync(kFull, own4.y, 1);
+        nxt2 = __shfl_down_sync(kFull, own4.z, 1);
+      }
       if (i0 < row1) {
         const unsigned short* mrow =
             reinterpret_cast<const unsigned short*>(st + s_lay.mask_f) + (base - (base & ~7)) + 4 * tid;
         const uint2 mu = *reinterpret_cast<const uint2*>(mrow);
         const unsigned m0 = mu.x & 0xffffu, m1 = mu.x >> 16, m2 = mu.y & 0xffffu, m3 = mu.y >> 16;
         // x[i0 + t] for t = -3 .. 6
-        const float wm3 = lane ? prv1 : ownp[-3], wm2 = lane ? prv2 : ownp[-2], wm1 = lane ? prv3 : ownp[-1];
-        const float w4 = lane != 31 ? nxt0 : ownp[4], w5 = lane != 31 ? nxt1 : ownp[5];
-        const float w6 = lane != 31 ? nxt2 : ownp[6];
+        // x[i0 - 1] and x[i0 + 4]: the neighbouring lanes' quads, or shared memory at a warp's ends
+        float wm1 = prv3, w4 = nxt0;
+        if (lane == 0) wm1 = ownp[-1];
+        if (lane == 31) w4 = ownp[4];
         const float w0 = own4.x, w1 = own4.y, w2 = own4.z, w3 = own4.w;
-        auto pick = [&](int t) {   // x[i0 + t], -3 <= t <= 6
-          return t == -3 ? wm3 : t == -2 ? wm2 : t == -1 ? wm1 : t == 0 ? w0 : t == 1 ? w1 : t == 2 ? w2
-               : t == 3 ? w3 : t == 4 ? w4 : t == 5 ? w5 : w6;
+        auto pick = [&](int t) {   // x[i0 + t], -3 <= t <= 6 (general offsets)
+          return t == -3 ? (lane ? prv1 : ownp[-3]) : t == -2 ? (lane ? prv2 : ownp[-2]) : t == -1 ? wm1
+               : t == 0 ? w0 : t == 1 ? w1 : t == 2 ? w2 : t == 3 ? w3 : t == 4 ? w4
+               : t == 5 ? (lane != 31 ? nxt1 : ownp[5]) : (lane != 31 ? nxt2 : ownp[6]);
         };
         float4 sv = own4;
         if (j > 1) sv = *reinterpret_cast<const float4*>(st + s_lay.src_f + 4 * tid);

@@ -70,3 +70,25 @@ def test_default_options_and_argument_errors(lib):
     assert b"NULL" in lib.pbicgstab_last_error()
     assert lib.pbicgstab_destroy(None) == 0
     assert lib.pbicgstab_solve(None, None, None, None) == _capi.PBCG_INVALID_ARG
+
+
+def test_batched_neumann_degree_checked_on_the_host(lib):
+    """A Neumann batch needs a degree in [1, 8]; the check runs before any CUDA call."""
+    import numpy as np
+    from paper_1809_01948_gb300 import _capi
+    off = np.array([0, 4], dtype=np.int64)
+    dummy = np.zeros(16, dtype=np.float64)
+    bt = _capi.Batch()
+    bt.n_sys, bt.val_dtype = 1, _capi.F64
+    bt.row_off = off.ctypes.data_as(C.c_void_p)
+    bt.nnz_off = off.ctypes.data_as(C.c_void_p)
+    bt.row_ptr = bt.col = bt.val = dummy.ctypes.data_as(C.c_void_p)
+    o = _capi.Options()
+    assert lib.pbicgstab_default_options(C.byref(o)) == 0
+    ctx = C.c_void_p()
+    for degree in (0, 9):
+        bt.precond, bt.degree = 2, degree
+        assert lib.pbicgstab_batch_create(C.byref(ctx), C.byref(bt), C.byref(o), None) == _capi.PBCG_INVALID_ARG
+        assert b"degree" in lib.pbicgstab_last_error()
+    bt.precond = 3   # no such preconditioner
+    assert lib.pbicgstab_batch_create(C.byref(ctx), C.byref(bt), C.byref(o), None) == _capi.PBCG_INVALID_ARG

@@ -196,3 +196,40 @@ def test_batched_streaming_cluster_build_equals_64_register_build():
     s4, _, _ = _batch_solver(bp, build="stream", precision="mixed", grid_blocks=8, block_threads=256)
     with pytest.raises(pb.PBCGError):   # a fixed shape with one block per system
         s4.solve(b)
+
+
+def test_batched_neumann_fp64_equals_single_solver():
+    """Neumann degree 2 in the batched solver: the same answers as the single-system solver."""
+    from gpu_common import make_solver, gpu_solve
+    bp = tp.problem_batched_banded(nsys=5, n_lo=400, n_hi=2500, band=40)
+    s, c, b = _batch_solver(bp, precond="neumann", degree=2, precision="fp64", tol=1e-12, max_it=500,
+                            rr_period=50)
+    x, info = s.solve(b)
+    x = x.cpu().numpy()
+    assert info["n_ok"] == 5, info["status"]
+    for k, sysk in enumerate(bp.systems):
+        single = make_solver(tp.Problem("s", sysk.A, sysk.b, sysk.x0, None, precond="neumann", degree=2, fmt="csr"),
+                             tol=1e-12, max_it=500, rr_period=50)
+        xs, res, _, _ = gpu_solve(single, sysk.b)
+        xk = x[c["row_off"][k]:c["row_off"][k + 1]]
+        assert res.status == 0
+        assert np.linalg.norm(xk - xs) <= 1e-10 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_batched_neumann_mixed_matches_oracle(cluster):
+    bp = tp.problem_batched_banded(nsys=12, n_lo=60, n_hi=3000, band=64)
+    s, c, b = _batch_solver(bp, precond="neumann", degree=2, precision="mixed", tol=1e-8, max_it=500,
+                            rr_theta=1e-3, cluster_blocks=cluster)
+    x, info = s.solve(b)
+    x = x.cpu().numpy()
+    assert info["n_ok"] == 12, info["status"]
+    for k, sysk in enumerate(bp.systems):
+        xk = x[c["row_off"][k]:c["row_off"][k + 1]]
+        A = sysk.A.to_scipy(np.float64)
+        true = np.linalg.norm(sysk.b - A @ xk) / np.linalg.norm(sysk.b)
+        assert true <= 1e-8 and abs(true - info["rel_res_true"][k]) <= 1e-3 * true + 1e-18
+        ref = oracle.pbicgstab(A, sysk.b, precond="neumann", degree=2, tol=1e-8, maxit=500, mixed=True,
+                               rr_theta=1e-3)
+        assert ref.status == oracle.Status.OK
+        assert int(info["iterations"][k]) <= 1.5 * ref.iterations + 5
