@@ -293,9 +293,10 @@ class BatchSolver:
 
     ``row_off``/``nnz_off``: host int64 arrays (n_sys + 1); ``row_ptr`` (local per
     system, concatenated: n_k + 1 entries each), ``col`` (local indices), ``val``:
-    CUDA tensors.  grid_blocks = block_threads = 0 lets the library autotune.  ``build``:
-    "auto", "regs64" (the 64-register kernels) or "stream" (the 40-register cluster
-    kernel; mixed precision).
+    CUDA tensors.  ``precond``: "none", "jacobi" or "neumann" (with ``degree`` 1..8), the
+    same for every system.  grid_blocks = block_threads = 0 lets the library autotune.
+    ``build``: "auto", "regs64" (the 64-register kernels) or "stream" (the 40-register
+    cluster kernel; mixed precision).
     """
 
     def __init__(self, row_off, nnz_off, row_ptr, col, val, precond: str = "jacobi", degree: int = 0,
