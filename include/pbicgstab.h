@@ -192,12 +192,12 @@ typedef struct pbcg_options {
   int32_t staged_sweeps;   /* single-system mixed solve with the four-row kernels and a
                               Neumann preconditioner on stencil storage: the Jacobi sweeps
                               of the preconditioner read their operands from shared-memory
-                              stages that bulk copies (TMA) fill three trips ahead, instead
-                              of from registers (same products in the same order).  0 =
+                              stages that bulk copies (TMA) fill a trip ahead, instead of
+                              from registers (same products in the same order).  0 =
                               automatic (on when a sweep's operands, 14 bytes per row,
                               exceed L2), > 0 = on, < 0 = off.  Ignored where it does not
-                              apply (block_threads a multiple of 32; offsets beyond 4 x
-                              block_threads rows multiples of 4; three stages must fit the
+                              apply (block_threads a multiple of 32; offsets beyond 8 x
+                              block_threads rows multiples of 4; two stages must fit the
                               block's shared memory)                                    */
 } pbcg_options;
 

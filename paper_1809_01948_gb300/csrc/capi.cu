@@ -386,8 +386,8 @@ static int kernel_threads(const pbcg_ctx* c, bool vec) {
   return streaming(c) ? pbcg::SolverLaunch<float, true>::kThreads : pbcg::SolverLaunch<double, false>::kThreads;
 }
 
-// Dynamic shared memory of the staged Neumann sweeps (options.staged_sweeps): three stages
-// of the layout stage_layout gives for a block's 4 x threads rows; 0 where they do not
+// Dynamic shared memory of the staged Neumann sweeps (options.staged_sweeps): two stages
+// of the layout stage_layout gives for a block's 8 x threads rows; 0 where they do not
 // apply (another kernel build, an offset the layout cannot stage, or no room beside the
 // kernel's static shared memory).  Automatic: where a sweep's operands (three FP32 vectors
 // and the masks, 14 bytes per row) exceed L2 — measured 12% faster per sweep on the 3D
@@ -399,9 +399,9 @@ size_t staged_bytes(const pbcg_ctx* c, int threads, bool vec) {
   if (c->opt.staged_sweeps == 0 && 14.0 * (double)c->n <= (double)l2_bytes()) return 0;
   const pbcg::MatView<float> v = make_stencil_view<float>(c, false);
   pbcg::StageLayout L;
-  pbcg::stage_layout(L, v.off, v.ndiag, 4 * threads);
+  pbcg::stage_layout(L, v.off, v.ndiag, 8 * threads);
   if (!L.ok) return 0;
-  const size_t bytes = (size_t)3 * (size_t)L.stage_f * sizeof(float);
+  const size_t bytes = (size_t)2 * (size_t)L.stage_f * sizeof(float);
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, kernel_ptr<float>(c, vec)) != cudaSuccess) return 0;
   int dev = 0, optin = 0;

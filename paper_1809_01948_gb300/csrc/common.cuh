@@ -332,14 +332,15 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Shared-memory layout of one stage of the staged stencil sweeps (four rows per thread, R =
-// 4 x threads rows per trip), the same on the host (dynamic shared memory size) and the
-// device: a near window of the gathered vector, rows [base - H, base + R + H) with H the
-// largest offset of magnitude <= R rounded up to 4 (at least 4); one R-row window per
-// farther offset (at base + offset, which must be a multiple of 4); the R own rows of the
-// source vector; R + 8 row masks from the multiple of 8 at or below base (16-byte bulk
-// copies; the mask array is padded to a multiple of 8 rows plus 8).  Sizes in floats;
-// every part starts on a 16-byte boundary.
+// Shared-memory layout of one stage of the staged stencil sweeps (two quads of four rows
+// per thread, R = 8 x threads rows per trip), the same on the host (dynamic shared memory
+// size) and the device: a near window of the gathered vector, rows [base - H, base + R + H)
+// with H the largest offset of magnitude <= R rounded up to 4 (at least 4); one R-row window
+// per farther offset (at base + offset, which must be a multiple of 4); R + 8 row masks from
+// the multiple of 8 at or below base (16-byte bulk copies; the mask array is padded to a
+// multiple of 8 rows plus 8).  The source vector's own rows are read from global memory (one
+// coalesced 16-byte load per quad), which leaves the L1 share of the unified cache to the
+// other passes.  Sizes in floats; every part starts on a 16-byte boundary.
 struct StageLayout {
   int R, H, nfar;
   int far[kMaxDiag];
@@ -365,7 +366,7 @@ __host__ __device__ inline void stage_layout(StageLayout& L, const int* off, int
   if (L.H < 4) L.H = 4;   // the sweep reads up to 3 rows beyond a warp's first and last quad
   if (R % 8 != 0) L.ok = 0;
   L.src_f = (R + 2 * L.H) + L.nfar * R;
-  L.mask_f = L.src_f + R;
+  L.mask_f = L.src_f;   // the source rows are read from global memory
   L.stage_f = L.mask_f + (R + 8) / 2;    // R + 8 16-bit masks
 }
 

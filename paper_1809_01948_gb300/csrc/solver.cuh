@@ -71,7 +71,7 @@ struct SolverParams {
   int strided;          // grid team row order: 1 grid-stride, 0 one contiguous chunk per block
   int prefetch;         // > 0: request the operands of the row sweep this many trips ahead into L2
   int staged;           // > 0: the four-row FP32 Neumann sweeps stage their operands in dynamic
-                        // shared memory (the kernel's launch provides three stages)
+                        // shared memory (the kernel's launch provides two stages)
   int overlap;          // 1: compute the next SpMV on a block's interior rows inside each grid
                         // barrier (chunked row order, no Neumann); 0: plain barriers
   int halo;             // max |col - row| of A: rows farther than this from a block's chunk
@@ -300,14 +300,15 @@ __device__ __forceinline__ T minv_local(const SolverParams<T, VR>& p, T v, int i
   return (p.prec == 1 && !SCALAR) ? T(dinv_at(p, i) * v) : v;
 }
 
-// One Jacobi sweep of the Neumann polynomial on four rows per thread with the operands
-// staged in shared memory: out = D^{-1}src + D^{-1}(src - V src) (j = 1, V = A D^{-1}) or
-// out = prev + D^{-1}(src - V prev) (j > 1, V = A), the same per-row products in the same
-// order as the register form.  Each block walks its trips (rows base .. base+R-1) through an
-// S-stage pipeline: thread 0 moves the windows of trip k+S-1 with bulk copies (TMA, one
-// instruction per contiguous window, completing on the stage's mbarrier) while the block
-// computes trip k from shared memory, so the loads wait in the copy engine rather than in
-// registers.  128-bit shared reads at a 16-byte thread stride are conflict-free; the
+// One Jacobi sweep of the Neumann polynomial on two quads of four rows per thread with the
+// operands staged in shared memory: out = D^{-1}src + D^{-1}(src - V src) (j = 1,
+// V = A D^{-1}) or out = prev + D^{-1}(src - V prev) (j > 1, V = A), the same per-row
+// products in the same order as the register form.  Each block walks its trips (rows
+// base .. base+R-1, R = 8 x threads) through an S-stage pipeline: thread 0 moves the windows
+// of trip k+S-1 with bulk copies (TMA, one instruction per contiguous window, completing on
+// the stage's mbarrier) while the block computes trip k from shared memory, so the loads
+// wait in the copy engine rather than in registers; two quads per thread halve the per-trip
+// waits and barriers.  128-bit shared reads at a 16-byte thread stride are conflict-free; the
 // couplings within +-3 rows come from the own quad and the neighbouring lanes' quads
 // (shuffles), the lanes at a warp's ends read the one value beyond it from shared memory.
 // A stage wait that runs past timeout_ns sets the error flag; the block then waits (bounded)
@@ -325,7 +326,7 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
   __shared__ __align__(8) unsigned long long s_bar[S];
   __shared__ int s_fail;
   if (tid == 0) {
-    stage_layout(s_lay, p.Au.off, p.Au.ndiag, 4 * (int)blockDim.x);
+    stage_layout(s_lay, p.Au.off, p.Au.ndiag, 8 * (int)blockDim.x);
     for (int q = 0; q < S; ++q) mbar_init(&s_bar[q], 1);
     fence_proxy_async_smem();
     fence_proxy_async_global();   // the previous sweep's plain stores, before bulk reads
@@ -343,8 +344,11 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
     }
     s_base[tid] = base;
   }
+  // two quads per thread per trip: rows base + q*4*blockDim + 4*tid, q = 0, 1
+  const int tfirst = p.strided ? 8 * (int)blockIdx.x * (int)blockDim.x : team.first;
+  const int tstride = p.strided ? 8 * (int)gridDim.x * (int)blockDim.x : 8 * (int)blockDim.x;
   int ntrips = 0;
-  for (int b = team.first4; b < row1; b += team.stride4) ++ntrips;
+  for (int b = tfirst; b < row1; b += tstride) ++ntrips;
   // V's offsets in one of the stencil patterns: the products of a trip then carry no
   // offset tests
   const int pat = V.pattern;
@@ -353,7 +357,7 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
   auto issue = [&](int k) {
     float* st = buf + (size_t)(k % S) * s_lay.stage_f;
     unsigned long long* bar = &s_bar[k % S];
-    const int base = team.first4 + k * team.stride4;
+    const int base = tfirst + k * tstride;
     const int mlo = base & ~7;
     const int mhi = min(mlo + R + 8, nmask);
     unsigned bytes = 0;
@@ -367,7 +371,6 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
       };
       win(st, gin, base - H, nearw);
       for (int f = 0; f < s_lay.nfar; ++f) win(st + nearw + f * R, gin, base + s_lay.far[f], R);
-      if (j > 1) win(st + s_lay.src_f, src, base, R);
       if (go) bulk_copy_g2s(st + s_lay.mask_f, p.Au.mask + mlo, (unsigned)(mhi - mlo) * 2u, bar);
       else bytes += (unsigned)(mhi - mlo) * 2u;
     }
@@ -383,9 +386,11 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
     if (!ok) s_fail = 1;
     if (ok) {
       const float* st = buf + (size_t)(k % S) * s_lay.stage_f;
-      const int base = team.first4 + k * team.stride4;
-      const int i0 = base + 4 * tid;
-      const float* ownp = st + H + 4 * tid;
+      const int base = tfirst + k * tstride;
+      for (int qd = 0; qd < 2; ++qd) {
+      const int qo = qd * 4 * (int)blockDim.x;
+      const int i0 = base + qo + 4 * tid;
+      const float* ownp = st + H + qo + 4 * tid;
       const float4 own4 = *reinterpret_cast<const float4*>(ownp);
       const float prv3 = __shfl_up_sync(kFull, own4.w, 1);
       const float nxt0 = __shfl_down_sync(kFull, own4.x, 1);
@@ -398,7 +403,7 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
       }
       if (i0 < row1) {
         const unsigned short* mrow =
-            reinterpret_cast<const unsigned short*>(st + s_lay.mask_f) + (base - (base & ~7)) + 4 * tid;
+            reinterpret_cast<const unsigned short*>(st + s_lay.mask_f) + (base - (base & ~7)) + qo + 4 * tid;
         const uint2 mu = *reinterpret_cast<const uint2*>(mrow);
         const unsigned m0 = mu.x & 0xffffu, m1 = mu.x >> 16, m2 = mu.y & 0xffffu, m3 = mu.y >> 16;
         // x[i0 + t] for t = -3 .. 6
@@ -413,7 +418,7 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
                : t == 5 ? (lane != 31 ? nxt1 : ownp[5]) : (lane != 31 ? nxt2 : ownp[6]);
         };
         float4 sv = own4;
-        if (j > 1) sv = *reinterpret_cast<const float4*>(st + s_lay.src_f + 4 * tid);
+        if (j > 1) sv = *reinterpret_cast<const float4*>(src + i0);   // own rows: one coalesced load
         float a0 = V.unit_diag ? w0 : 0.f, a1 = V.unit_diag ? w1 : 0.f;
         float a2 = V.unit_diag ? w2 : 0.f, a3 = V.unit_diag ? w3 : 0.f;
         // offset d's products; with the offset count known at compile time (5: 2D, 7: 3D
@@ -429,10 +434,10 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
           else if (off == 0) { e0 = w0; e1 = w1; e2 = w2; e3 = w3; }
           else if (off >= -3 && off <= 3) { e0 = pick(off); e1 = pick(off + 1); e2 = pick(off + 2); e3 = pick(off + 3); }
           else if ((off & 3) == 0) {
-            const float4 v4 = *reinterpret_cast<const float4*>(st + s_base[d] + 4 * tid);
+            const float4 v4 = *reinterpret_cast<const float4*>(st + s_base[d] + qo + 4 * tid);
             e0 = v4.x; e1 = v4.y; e2 = v4.z; e3 = v4.w;
           } else {
-            const float* ep = st + s_base[d] + 4 * tid;
+            const float* ep = st + s_base[d] + qo + 4 * tid;
             e0 = ep[0]; e1 = ep[1]; e2 = ep[2]; e3 = ep[3];
           }
           if ((m0 >> bit) & 1u) a0 = fma(c, e0, a0);
@@ -450,7 +455,7 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
           else if constexpr (K == 2) { e0 = w0; e1 = w1; e2 = w2; e3 = w3; }
           else if constexpr (K == 3) { e0 = w1; e1 = w2; e2 = w3; e3 = w4; }
           else {
-            const float4 v4 = *reinterpret_cast<const float4*>(st + s_base[d] + 4 * tid);
+            const float4 v4 = *reinterpret_cast<const float4*>(st + s_base[d] + qo + 4 * tid);
             e0 = v4.x; e1 = v4.y; e2 = v4.z; e3 = v4.w;
           }
           if ((m0 >> bit) & 1u) a0 = fma(c, e0, a0);
@@ -487,6 +492,7 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
         }
         st4(out, i0, o);
       }
+      }   // qd
     }
     __syncthreads();   // the stage is refilled for trip k + S; s_fail is settled
     if (s_fail) break;
@@ -518,7 +524,7 @@ __device__ bool neumann_apply(const SolverParams<T, VR>& p, Team& team, const T*
     if constexpr (VEC && std::is_same<T, float>::value) {
       if (p.staged && !src1) {
         extern __shared__ __align__(16) float pbcg_stage_smem[];
-        staged_sweep<3>(p, team, pbcg_stage_smem, j, src0, prev0, out0);
+        staged_sweep<2>(p, team, pbcg_stage_smem, j, src0, prev0, out0);
         if (!team.sync()) return false;
         prev0 = out0;
         continue;

@@ -116,12 +116,12 @@ def test_four_row_kernels_run_where_they_apply():
 
 
 STAGED = {
-    # name: (problem, block_threads, staged): a block stages 4 x block_threads rows per trip
+    # name: (problem, block_threads, staged): a block stages 8 x block_threads rows per trip
     "3d_40_near": (lambda: tp.problem_convdiff3d(40), 0, True),       # offsets 1, 40, 1600 within a trip
-    "3d_40_far": (lambda: tp.problem_convdiff3d(40), 256, True),      # 1600 beyond a trip: its own window
-    "3d_34_far": (lambda: tp.problem_convdiff3d(34), 128, True),      # 34 near, 1156 far
-    "2d_130_near_odd": (lambda: tp.problem_convdiff2d(130), 64, True),    # 130 near, not a multiple of 4
-    "2d_130_far_odd": (lambda: tp.problem_convdiff2d(130), 32, False),    # 130 beyond a trip, unaligned
+    "3d_40_far": (lambda: tp.problem_convdiff3d(40), 128, True),      # 1600 beyond a trip: its own window
+    "3d_34_far": (lambda: tp.problem_convdiff3d(34), 64, True),       # 34 near, 1156 far
+    "2d_130_near_odd": (lambda: tp.problem_convdiff2d(130), 32, True),    # 130 near, not a multiple of 4
+    "2d_262_far_odd": (lambda: tp.problem_convdiff2d(262), 32, False),    # 262 beyond a trip, unaligned
     "2d_512_chunked": (lambda: tp.problem_convdiff2d(512), 0, True),      # chunked row order
 }
 
