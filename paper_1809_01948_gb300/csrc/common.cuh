@@ -327,6 +327,11 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+// Bring a contiguous range into L2 without waiting for it (bytes: a multiple of 16; src
+// 16-byte aligned).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 // Generic-proxy writes (earlier plain stores, seen through a grid barrier) before async-proxy
 // reads of global memory; an initialised mbarrier before the async proxy signals it.
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }

@@ -371,6 +371,10 @@ __device__ void staged_sweep(const SolverParams<float, VR>& p, const Team& team,
       };
       win(st, gin, base - H, nearw);
       for (int f = 0; f < s_lay.nfar; ++f) win(st + nearw + f * R, gin, base + s_lay.far[f], R);
+      if (go && j > 1) {   // the source rows, read from global memory by the trip: into L2 now
+        const int a1 = min(base + R, n);
+        if (a1 > base) bulk_prefetch_l2(src + base, (unsigned)(a1 - base) * 4u);
+      }
       if (go) bulk_copy_g2s(st + s_lay.mask_f, p.Au.mask + mlo, (unsigned)(mhi - mlo) * 2u, bar);
       else bytes += (unsigned)(mhi - mlo) * 2u;
     }
